@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark: bulk AES-ECB on GB300, one JSON line on stdout (rank 0).
+
+Workload (one "step"): AES-128, AES-192 and AES-256, one seeded random key each,
+a 1 GiB device-resident buffer of seeded uniform random bytes per key size;
+encrypt the buffer in one launch, then decrypt the ciphertext in one launch --
+six launches, 6 GiB of plaintext-equivalent bytes per step and GPU.  The buffers
+(1 GiB) are larger than the 129 MB L2, so no flush is needed between steps.
+
+  value     GB/s (1e9 B/s) over all ranks: bytes all ranks processed / max-over-ranks
+            device time of the K timed steps (CUDA events on the launching stream).
+  roofline  the dominant launch (largest share of step time) against the
+            shared-memory lookup bound of Eq. 1 (16*Nr conflict-free 4-byte lookups
+            per block, 32 per clock per SM), in plaintext GB/s.
+  e2e       the same workload through the same C ABI calls with the data in pinned
+            host memory: host->device copy, the cipher launch, device->host copy,
+            all inside the timed region.
+  cpu_baseline  the CPU oracle (plain byte-oriented AES) on all host cores on a
+            bounded 64 MiB sample of each of the six operations (rank 0, N=1 only).
+
+--impl reference times the CPU oracle as the reference arm (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "AES-128/256 ECB GB/s on 1 GB300 (% of roofline); batched GB/s and p99 latency"
+WORKLOAD = "aes-ecb encrypt+decrypt, 1 GiB device-resident buffer per key size (128/192/256), one launch per op"
+BITS = (128, 192, 256)
+NR = {128: 10, 192: 12, 256: 14}
+GiB = 1 << 30
+MiB = 1 << 20
+LOOKUPS_PER_CLK_PER_SM = 32  # 32 banks x 4 B: one conflict-free 32-bit lookup per lane per clock
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--buffer-mib", type=int, default=1024, help="bytes per key size (default 1 GiB)")
+    p.add_argument("--e2e-steps", type=int, default=0, help="0 = max(3, steps // 20)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--kernel", choices=("table", "bitsliced"), default="table")
+    return p.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_fingerprint() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1201_0398_gb300", "csrc")
+    for name in ("ecb_table.cu", "aes_tables.h", "gbaes_internal.h"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic(kernel_key: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    fp = kernel_fingerprint()
+    for line in lines:
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == fp and parts[1] == kernel_key:
+            return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """Samples SM clock and throttle reasons with nvidia-smi while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.device_index = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"gbaes_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            import torch
+
+            uuid = str(torch.cuda.get_device_properties(self.device_index).uuid)
+            ident = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+        except Exception:
+            ident = str(self.device_index)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", ident], stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]) if f[3] not in ("[N/A]", "N/A") else None, f[5:9],
+                             f[4]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r for r in rows if r[2] is None or r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "power_w_max": max((r[2] or 0.0) for r in rows)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ reference arm
+
+
+def oracle_rate(sample_bytes: int, seed_offset: int = 0):
+    """Times the CPU oracle on sample_bytes of each of the six operations.
+    Returns (bytes, seconds, threads)."""
+    import numpy as np
+
+    import oracle
+    from paper_1201_0398_gb300 import workloads
+
+    threads = os.cpu_count() or 1
+    total_b, total_t = 0, 0.0
+    for bits in BITS:
+        key = workloads.random_key(workloads.SEED_BULK[bits], bits)
+        data = workloads.host_bytes(workloads.SEED_BULK[bits] + seed_offset, sample_bytes)
+        t0 = time.perf_counter()
+        ct = oracle.ecb(key, bits, data, nthreads=threads)
+        pt = oracle.ecb(key, bits, ct, decrypt=True, nthreads=threads)
+        total_t += time.perf_counter() - t0
+        total_b += 2 * sample_bytes
+        if not np.array_equal(pt, data):
+            raise RuntimeError("oracle round trip failed")
+    return total_b, total_t, threads
+
+
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    per_step = 2 * MiB
+    for i in range(args.warmup):
+        oracle_rate(per_step, seed_offset=1000 + i)
+    tb, tt = 0, 0.0
+    threads = os.cpu_count() or 1
+    for i in range(args.steps):
+        b, t, threads = oracle_rate(per_step, seed_offset=i)
+        tb += b
+        tt += t
+    value = tb / tt / 1e9
+    sample = (f"each step: the first {per_step // MiB} MiB of each of the six operations "
+              f"(AES-128/192/256 encrypt + decrypt), oracle on {threads} host threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded uniform random bytes and keys)",
+        "config": {"workload": WORKLOAD, "sample_bytes_per_op": per_step},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# --------------------------------------------------------------------- our arm
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1201_0398_gb300 as g
+    from paper_1201_0398_gb300 import workloads
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g.load()
+    kernel = g.KERNEL_TABLE if args.kernel == "table" else g.KERNEL_BITSLICED
+    size = args.buffer_mib * MiB
+    nblocks = size // 16
+    stream = torch.cuda.current_stream(dev)
+    keys, x, c, p = {}, {}, {}, {}
+    for bits in BITS:
+        keys[bits] = g.Key(workloads.random_key(workloads.SEED_BULK[bits], bits))
+        x[bits] = workloads.device_bytes(workloads.SEED_BULK[bits] + 97 * rank, size, device=dev)
+        c[bits] = torch.empty_like(x[bits])
+        p[bits] = torch.empty_like(x[bits])
+    ops = [(bits, dec) for bits in BITS for dec in (False, True)]
+
+    def launch(bits, dec):
+        src, dst = (c[bits], p[bits]) if dec else (x[bits], c[bits])
+        g.ecb_ex(keys[bits], src, dst, decrypt=dec, kernel=kernel, stream=stream)
+
+    for _ in range(args.warmup):
+        for bits, dec in ops:
+            launch(bits, dec)
+    torch.cuda.synchronize()
+    for bits in BITS:  # sanity (untimed): decrypt(encrypt(x)) == x on the device
+        if not torch.equal(p[bits], x[bits]):
+            raise RuntimeError(f"round trip failed for AES-{bits}")
+
+    ev = {op: [] for op in ops}
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    props = torch.cuda.get_device_properties(dev)
+    with ClockSampler(local) as clocks:
+        barrier(world)
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(args.steps):
+            for op in ops:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                launch(*op)
+                e1.record(stream)
+                ev[op].append((e0, e1))
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    elapsed_s = start.elapsed_time(end) / 1e3
+    elapsed_max = max_over_ranks(world, elapsed_s)
+    clk = clocks.summary()
+    bytes_per_step = len(ops) * size
+    value = world * args.steps * bytes_per_step / elapsed_max / 1e9
+
+    peaks, peak_kind = measured_peaks()
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    sms = props.multi_processor_count
+    op_stats = {}
+    for (bits, dec), pairs in ev.items():
+        ms = statistics.mean(a.elapsed_time(b) for a, b in pairs)
+        gbs = size / (ms / 1e3) / 1e9
+        r_smem = sms * LOOKUPS_PER_CLK_PER_SM * f_max / NR[bits] / 1e9
+        op_stats[f"aes{bits}_{'dec' if dec else 'enc'}"] = {
+            "ms": ms, "gbs": gbs, "smem_roofline_gbs": r_smem, "frac": gbs / r_smem,
+            "hbm_frac": 2 * gbs / float(peaks["hbm_gbs"])}
+    dom_name, dom = max(op_stats.items(), key=lambda kv: kv[1]["ms"])
+    bits_dom = int(dom_name[3:6])
+    dec_dom = dom_name.endswith("dec")
+    ktpl = f"table_kernel<{NR[bits_dom]},{1 if dec_dom else 0},2>"
+    traffic = dram_traffic(ktpl) if kernel == g.KERNEL_TABLE else None
+    clock_frac = None
+    if clk.get("sm_mhz"):
+        r_clk = sms * LOOKUPS_PER_CLK_PER_SM * clk["sm_mhz"] * 1e6 / NR[bits_dom] / 1e9
+        clock_frac = dom["gbs"] / r_clk
+    roofline = {
+        "bound": "smem", "achieved": dom["gbs"], "peak": dom["smem_roofline_gbs"], "unit": "GB/s",
+        "frac": dom["frac"], "traffic": traffic, "kernel": ktpl if kernel == g.KERNEL_TABLE else "bitsliced",
+        "peak_basis": (f"{sms} SMs x {LOOKUPS_PER_CLK_PER_SM} lookups/clk x {f_max / 1e6:.0f} MHz "
+                       f"({peak_kind} sm_max_mhz) / {NR[bits_dom]} lookups per plaintext byte"),
+        "frac_at_measured_clock": clock_frac,
+        "hbm": {"achieved": 2 * dom["gbs"], "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "frac": dom["hbm_frac"], "peak_kind": f"{peak_kind} hbm_gbs (copy)"},
+    }
+
+    # ---- e2e: pinned host buffers, copies inside the timed region
+    e2e_steps = args.e2e_steps or max(3, args.steps // 20)
+    xh = {bits: torch.empty(size, dtype=torch.uint8, pin_memory=True) for bits in BITS}
+    ch = {bits: torch.empty(size, dtype=torch.uint8, pin_memory=True) for bits in BITS}
+    ph = torch.empty(size, dtype=torch.uint8, pin_memory=True)
+    for bits in BITS:
+        xh[bits].copy_(x[bits])
+    dbuf_in, dbuf_out = torch.empty_like(x[128]), torch.empty_like(x[128])
+
+    def e2e_step():
+        for bits in BITS:
+            dbuf_in.copy_(xh[bits], non_blocking=True)
+            g.ecb_ex(keys[bits], dbuf_in, dbuf_out, decrypt=False, kernel=kernel, stream=stream)
+            ch[bits].copy_(dbuf_out, non_blocking=True)
+            dbuf_in.copy_(ch[bits], non_blocking=True)
+            g.ecb_ex(keys[bits], dbuf_in, dbuf_out, decrypt=True, kernel=kernel, stream=stream)
+            ph.copy_(dbuf_out, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if not torch.equal(ph, xh[256]):
+        raise RuntimeError("e2e round trip failed")
+    barrier(world)
+    torch.cuda.synchronize()
+    s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s2.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, s2.elapsed_time(e2) / 1e3)
+    e2e = {"value": world * e2e_steps * bytes_per_step / e2e_s / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": bytes_per_step, "d2h_bytes_per_step": bytes_per_step, "steps": e2e_steps,
+           "path": "pinned host -> device copy, C-ABI ECB launch, device -> pinned host copy, serial on one stream"}
+    del xh, ch, ph, dbuf_in, dbuf_out
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = 64 * MiB
+        b, t, threads = oracle_rate(sample)
+        cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {sample // MiB} MiB of each of the six operations (AES-128/192/256 enc+dec), "
+                         f"{threads} host threads"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded uniform random bytes and keys)",
+            "config": {"workload": WORKLOAD, "buffer_bytes": size, "nblocks_per_op": nblocks,
+                       "kernel": args.kernel, "launches_per_step": len(ops), "sms": sms,
+                       "l2": "inputs larger than L2 (1 GiB > 129 MB), no flush",
+                       "parallelism": f"replicas x{world} (independent buffers per rank)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(ops) * args.steps,
+            "clocks": clk, "ops": op_stats,
+        }), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,150 @@
+/*
+ * gbaes -- bulk AES on NVIDIA GB300 (sm_103a): the C ABI.
+ *
+ * What it computes: the AES block cipher (FIPS-197; 128-bit blocks, 128/192/256-bit
+ * keys, 10/12/14 rounds) on many independent 16-byte blocks, as described in
+ * Section 2.1 of "AES Encryption and Decryption Using Direct3D 10 API" (Chiuta),
+ * with each round in the fused T-table form of Eq. 1 (SubBytes, ShiftRows and
+ * MixColumns folded into four 32-bit table lookups XORed with the round key),
+ * plus the parallel modes of Section 3 (ECB, CTR, CBC decryption).
+ *
+ * Conventions shared by every call:
+ *  - A block is 16 bytes read "exactly as found in memory" (Section 3): four
+ *    little-endian 32-bit words, byte 4c+r of the block is row r of column c.
+ *  - Data pointers named in/out are DEVICE pointers (cudaMalloc, torch CUDA
+ *    tensors, managed memory, or -- on systems where the GPU reads pageable host
+ *    memory -- host memory).  The caller owns them.  Each must be 16-byte
+ *    aligned (AES_ERR_ALIGN) and [ptr, ptr + 16*nblocks) must lie inside one
+ *    allocation the GPU can reach (AES_ERR_ARG otherwise); the library checks
+ *    this on the host before launching, so a bad pointer is an error code, not
+ *    a GPU fault.
+ *  - in == out (in place) is allowed unless a call says otherwise; any other
+ *    overlap of the two ranges is rejected (AES_ERR_ARG).
+ *  - nblocks == 0 returns AES_OK and launches nothing.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls that launch work are asynchronous on that stream and
+ *    return AES_OK once the work is queued; completion is observed through the
+ *    stream.  No call here synchronises the device unless it says so.
+ *  - Keys and IVs are HOST pointers, read during the call only.
+ *  - There is no padding (Section 2.1 leaves the padding values unspecified);
+ *    lengths are whole blocks.  There is no CPU fallback: without a usable
+ *    CUDA device, launching calls return AES_ERR_CUDA.
+ *  - On failure a call returns a negative AES_ERR_* code and records a message
+ *    that aes_last_error() returns (per thread).
+ */
+#ifndef GBAES_H_
+#define GBAES_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AES_OK 0
+#define AES_ERR_ARG (-1)     /* bad pointer, size, flag or overlapping ranges */
+#define AES_ERR_KEYSIZE (-2) /* bits not in {128, 192, 256} */
+#define AES_ERR_ALIGN (-3)   /* a data pointer is not 16-byte aligned */
+#define AES_ERR_CUDA (-4)    /* a CUDA runtime call or kernel launch failed */
+#define AES_ERR_BUDGET (-5)  /* request larger than a server's memory budget */
+#define AES_ERR_NOMEM (-6)   /* host or device allocation failed */
+#define AES_ERR_DEVICE (-7)  /* a kernel reported an error through its status word */
+#define AES_ERR_STATE (-8)   /* object used in the wrong state (e.g. closed server) */
+
+/* Kernel variants for aes_ecb_ex / aes_set_kernel. */
+#define AES_KERNEL_TABLE 0     /* Eq. 1 T-table kernel, tables in shared memory */
+#define AES_KERNEL_BITSLICED 1 /* Boolean-circuit S-box over bit planes of 32 blocks */
+
+/* Counter layouts for aes_ctr_xcrypt (Section 3, CTR mode). */
+#define AES_CTR_BE128 0     /* IV is one big-endian 128-bit integer (NIST SP 800-38A) */
+#define AES_CTR_LE32_CARRY 1 /* IV is four little-endian 32-bit words x,y,z,w; the
+                                block index is added to x with a carry into y, z, w
+                                (the counter of Section 3's CTR listing) */
+
+/* Opaque key context: the host copy of the expanded encryption schedule and of
+ * the equivalent-inverse decryption schedule.  Immutable after creation, so one
+ * context may be used from several threads and streams at once. */
+typedef struct aes_ctx aes_ctx;
+
+/* Key expansion (round keys K_i of Eq. 1; FIPS-197 KeyExpansion, which Section
+ * 2.1 defers to).  key: HOST pointer to bits/8 bytes; bits in {128,192,256}.
+ * Computes the (Nr+1) x 4-word encryption schedule and the decryption schedule
+ * of the equivalent inverse cipher (same round keys in reverse order, with
+ * InvMixColumns applied to rounds 1..Nr-1).  Needs no GPU.  Returns NULL on
+ * error (see aes_last_error()).  Free with aes_free_ctx. */
+aes_ctx* aes_expand_key(const uint8_t* key, int bits);
+
+/* Frees a context.  The caller must ensure no queued work still uses it (the
+ * launching calls copy the schedule into the launch, so a context may be freed
+ * as soon as the launching call has returned).  NULL is ignored. */
+void aes_free_ctx(aes_ctx* ctx);
+
+/* Key size in bits of a context (128/192/256), or AES_ERR_ARG. */
+int aes_ctx_bits(const aes_ctx* ctx);
+
+/* ECB encryption of nblocks independent blocks (Section 3: one block per
+ * pixel; Eq. 1 for rounds 1..Nr-1, an S-box-only last round).  in/out:
+ * device pointers, 16*nblocks bytes each; in == out allowed. */
+int aes_encrypt_ecb(const aes_ctx* ctx, const void* in, void* out, size_t nblocks, void* stream);
+
+/* ECB decryption (Section 2.1: the inverse cipher), run as the equivalent
+ * inverse cipher with inverse T-tables; same arguments as aes_encrypt_ecb. */
+int aes_decrypt_ecb(const aes_ctx* ctx, const void* in, void* out, size_t nblocks, void* stream);
+
+/* ECB with an explicit kernel choice, for benchmarking and tuning.
+ * decrypt: 0/1.  kernel: AES_KERNEL_*.  threads: CTA size, a multiple of 32 in
+ * [64, 1024] (0 = default).  blocks_per_thread: 1, 2 or 4 for the table kernel
+ * (0 = default; the bitsliced kernel always takes 32 blocks per thread). */
+int aes_ecb_ex(const aes_ctx* ctx, int decrypt, const void* in, void* out, size_t nblocks, int kernel,
+               int threads, int blocks_per_thread, void* stream);
+
+/* CTR mode (Section 3): out_i = in_i XOR E_K(counter(first_block + i)) for
+ * i < nblocks.  iv: HOST pointer to 16 bytes.  counter_kind: AES_CTR_*.  The
+ * counter arithmetic is modulo 2^128.  Encryption and decryption are the same
+ * call.  in == out allowed. */
+int aes_ctr_xcrypt(const aes_ctx* ctx, const uint8_t* iv, int counter_kind, uint64_t first_block, const void* in,
+                   void* out, size_t nblocks, void* stream);
+
+/* CBC decryption (Section 3, Eq. 2; the first block is chained to the IV on
+ * the GPU rather than on the CPU): out_i = D_K(in_i) XOR in_{i-1}, in_{-1} =
+ * iv (HOST pointer to 16 bytes).  To decrypt a long message in pieces, pass
+ * the last ciphertext block of the previous piece as iv.  in and out must not
+ * overlap at all (each output depends on two input blocks). */
+int aes_cbc_decrypt(const aes_ctx* ctx, const uint8_t* iv, const void* in, void* out, size_t nblocks, void* stream);
+
+/* Default kernel variant for aes_encrypt_ecb / aes_decrypt_ecb (process-wide;
+ * AES_KERNEL_TABLE at start).  Returns the previous variant or AES_ERR_ARG. */
+int aes_set_kernel(int which);
+
+/* Default launch shape of the table kernel for one (key size, direction):
+ * threads per CTA (multiple of 32, 64..1024) and blocks per thread (1/2/4).
+ * The autotuner calls this with the shape it measured fastest. */
+int aes_set_tuning(int bits, int decrypt, int threads, int blocks_per_thread);
+
+/* Reads (and with clear != 0 resets) the library's device status word on the
+ * current device: 0 when no kernel has reported an error.  Synchronises the
+ * device.  Returns the status (>= 0) or AES_ERR_CUDA. */
+int aes_device_status(int clear);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char* aes_last_error(void);
+
+/* ---------------------------------------------------------------- host only
+ * These run on the CPU alone (no GPU needed) and expose the library's own
+ * tables and schedules so their host logic can be tested without a device. */
+
+/* Writes the expanded schedules as little-endian words: enc_rk and dec_rk each
+ * receive 4*(Nr+1) uint32 (either may be NULL).  Returns Nr or a negative code. */
+int aes_key_schedule(const uint8_t* key, int bits, uint32_t* enc_rk, uint32_t* dec_rk);
+
+/* Copies the library's generated tables: Te0 and Td0 of Eq. 1 (256 words each;
+ * T_k = rotl(T_0, 8k)), the S-box and the inverse S-box (256 bytes each).  Any
+ * pointer may be NULL.  Returns AES_OK. */
+int aes_host_tables(uint32_t* te0, uint32_t* td0, uint8_t* sbox, uint8_t* inv_sbox);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBAES_H_ */

@@ -1,0 +1,268 @@
+"""gbaes: bulk AES on GB300 (sm_103a) -- Python binding of the C ABI in include/gbaes.h.
+
+This module only marshals arguments: torch CUDA tensors become device pointers,
+the current torch stream becomes a cudaStream_t, and error codes become
+``AesError``.  Every step of the cipher runs in the CUDA kernels of
+``libgbaes.so``; there is no CPU fallback, and every call raises if the library
+cannot be loaded.
+
+The cipher is AES (Section 2.1 of the paper) with rounds in the T-table form of
+Eq. 1; modes are those of Section 3 (ECB, CTR, CBC decryption).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "AesError",
+    "Key",
+    "load",
+    "encrypt_ecb",
+    "decrypt_ecb",
+    "ecb_ex",
+    "ctr_xcrypt",
+    "cbc_decrypt",
+    "set_kernel",
+    "set_tuning",
+    "device_status",
+    "key_schedule",
+    "host_tables",
+    "KERNEL_TABLE",
+    "KERNEL_BITSLICED",
+    "CTR_BE128",
+    "CTR_LE32_CARRY",
+]
+
+KERNEL_TABLE = 0
+KERNEL_BITSLICED = 1
+CTR_BE128 = 0
+CTR_LE32_CARRY = 1
+
+ERRORS = {
+    -1: "AES_ERR_ARG",
+    -2: "AES_ERR_KEYSIZE",
+    -3: "AES_ERR_ALIGN",
+    -4: "AES_ERR_CUDA",
+    -5: "AES_ERR_BUDGET",
+    -6: "AES_ERR_NOMEM",
+    -7: "AES_ERR_DEVICE",
+    -8: "AES_ERR_STATE",
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class AesError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+def library_path() -> str:
+    from . import _build
+
+    return _build.LIB
+
+
+def _declare(lib):
+    c = ctypes
+    vp, sz, u8p, u32p = c.c_void_p, c.c_size_t, c.POINTER(c.c_uint8), c.POINTER(c.c_uint32)
+    sig = {
+        "aes_expand_key": (vp, [u8p, c.c_int]),
+        "aes_free_ctx": (None, [vp]),
+        "aes_ctx_bits": (c.c_int, [vp]),
+        "aes_encrypt_ecb": (c.c_int, [vp, vp, vp, sz, vp]),
+        "aes_decrypt_ecb": (c.c_int, [vp, vp, vp, sz, vp]),
+        "aes_ecb_ex": (c.c_int, [vp, c.c_int, vp, vp, sz, c.c_int, c.c_int, c.c_int, vp]),
+        "aes_ctr_xcrypt": (c.c_int, [vp, u8p, c.c_int, c.c_uint64, vp, vp, sz, vp]),
+        "aes_cbc_decrypt": (c.c_int, [vp, u8p, vp, vp, sz, vp]),
+        "aes_set_kernel": (c.c_int, [c.c_int]),
+        "aes_set_tuning": (c.c_int, [c.c_int, c.c_int, c.c_int, c.c_int]),
+        "aes_device_status": (c.c_int, [c.c_int]),
+        "aes_last_error": (c.c_char_p, []),
+        "aes_key_schedule": (c.c_int, [u8p, c.c_int, u32p, u32p]),
+        "aes_host_tables": (c.c_int, [u32p, u32p, u8p, u8p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def load(build_if_missing: bool = True):
+    """Loads libgbaes.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import _build
+
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise AesError(-4, f"CUDA library not found at {path}; run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            _declare(lib)
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        msg = load().aes_last_error()
+        raise AesError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _u8p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _nblocks(t) -> int:
+    n = t.numel() * t.element_size()
+    if n % 16:
+        raise ValueError(f"buffer of {n} bytes is not a whole number of 16-byte blocks")
+    return n // 16
+
+
+def _ptr(t):
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Key:
+    """An expanded AES key (``aes_ctx``): encryption and decryption schedules."""
+
+    def __init__(self, key, bits: int | None = None):
+        k = np.ascontiguousarray(np.frombuffer(bytes(key), np.uint8) if isinstance(key, (bytes, bytearray))
+                                 else np.asarray(key, np.uint8))
+        bits = bits if bits is not None else 8 * k.size
+        if k.size != bits // 8:
+            raise ValueError(f"key has {k.size} bytes, expected {bits // 8}")
+        lib = load()
+        self._lib = lib
+        h = lib.aes_expand_key(_u8p(k), int(bits))
+        if not h:
+            _check(-2 if bits not in (128, 192, 256) else -1)
+        self._h = ctypes.c_void_p(h)
+        self.bits = bits
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.aes_free_ctx(h)
+            self._h = None
+
+
+def _out_like(x, out):
+    import torch
+
+    if out is None:
+        out = torch.empty_like(x)
+    if out.numel() * out.element_size() != x.numel() * x.element_size():
+        raise ValueError("out must have the same byte size as the input")
+    return out
+
+
+def encrypt_ecb(key: Key, x, out=None, stream=None):
+    """ECB encryption of a CUDA tensor (any dtype; its bytes are the blocks)."""
+    out = _out_like(x, out)
+    _check(load().aes_encrypt_ecb(key.handle, _ptr(x), _ptr(out), _nblocks(x), _stream_handle(stream)))
+    return out
+
+
+def decrypt_ecb(key: Key, x, out=None, stream=None):
+    """ECB decryption of a CUDA tensor."""
+    out = _out_like(x, out)
+    _check(load().aes_decrypt_ecb(key.handle, _ptr(x), _ptr(out), _nblocks(x), _stream_handle(stream)))
+    return out
+
+
+def ecb_ex(key: Key, x, out=None, decrypt=False, kernel=KERNEL_TABLE, threads=0, blocks_per_thread=0,
+           stream=None):
+    """ECB with an explicit kernel variant and launch shape."""
+    out = _out_like(x, out)
+    _check(load().aes_ecb_ex(key.handle, int(bool(decrypt)), _ptr(x), _ptr(out), _nblocks(x), int(kernel),
+                             int(threads), int(blocks_per_thread), _stream_handle(stream)))
+    return out
+
+
+def _iv(iv) -> np.ndarray:
+    v = np.ascontiguousarray(np.frombuffer(bytes(iv), np.uint8))
+    if v.size != 16:
+        raise ValueError("iv must be 16 bytes")
+    return v
+
+
+def ctr_xcrypt(key: Key, iv, x, out=None, kind=CTR_BE128, first_block=0, stream=None):
+    """CTR mode (Section 3): x XOR E_K(counter(first_block + i))."""
+    out = _out_like(x, out)
+    v = _iv(iv)
+    _check(load().aes_ctr_xcrypt(key.handle, _u8p(v), int(kind), int(first_block), _ptr(x), _ptr(out),
+                                 _nblocks(x), _stream_handle(stream)))
+    return out
+
+
+def cbc_decrypt(key: Key, iv, x, out=None, stream=None):
+    """CBC decryption (Section 3, Eq. 2)."""
+    out = _out_like(x, out)
+    v = _iv(iv)
+    _check(load().aes_cbc_decrypt(key.handle, _u8p(v), _ptr(x), _ptr(out), _nblocks(x), _stream_handle(stream)))
+    return out
+
+
+def set_kernel(which: int) -> int:
+    return _check(load().aes_set_kernel(int(which)))
+
+
+def set_tuning(bits: int, decrypt: bool, threads: int, blocks_per_thread: int) -> None:
+    _check(load().aes_set_tuning(int(bits), int(bool(decrypt)), int(threads), int(blocks_per_thread)))
+
+
+def device_status(clear: bool = False) -> int:
+    """The library's device status word (0 = no kernel reported an error). Synchronises."""
+    return _check(load().aes_device_status(int(bool(clear))))
+
+
+def key_schedule(key, bits: int):
+    """Host-side schedules (enc, dec) as (Nr+1, 4) uint32 arrays; needs no GPU."""
+    k = np.ascontiguousarray(np.frombuffer(bytes(key), np.uint8))
+    enc = np.zeros(60, np.uint32)
+    dec = np.zeros(60, np.uint32)
+    u32 = ctypes.POINTER(ctypes.c_uint32)
+    nr = _check(load().aes_key_schedule(_u8p(k), int(bits), enc.ctypes.data_as(u32), dec.ctypes.data_as(u32)))
+    return enc[: 4 * (nr + 1)].reshape(nr + 1, 4), dec[: 4 * (nr + 1)].reshape(nr + 1, 4)
+
+
+def host_tables():
+    """The library's generated tables (Te0, Td0, S-box, inverse S-box); needs no GPU."""
+    te0 = np.zeros(256, np.uint32)
+    td0 = np.zeros(256, np.uint32)
+    s = np.zeros(256, np.uint8)
+    si = np.zeros(256, np.uint8)
+    u32 = ctypes.POINTER(ctypes.c_uint32)
+    _check(load().aes_host_tables(te0.ctypes.data_as(u32), td0.ctypes.data_as(u32), _u8p(s), _u8p(si)))
+    return te0, td0, s, si
