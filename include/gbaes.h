@@ -12,12 +12,13 @@
  *  - A block is 16 bytes read "exactly as found in memory" (Section 3): four
  *    little-endian 32-bit words, byte 4c+r of the block is row r of column c.
  *  - Data pointers named in/out are DEVICE pointers (cudaMalloc, torch CUDA
- *    tensors, managed memory, or -- on systems where the GPU reads pageable host
- *    memory -- host memory).  The caller owns them.  Each must be 16-byte
- *    aligned (AES_ERR_ALIGN) and [ptr, ptr + 16*nblocks) must lie inside one
- *    allocation the GPU can reach (AES_ERR_ARG otherwise); the library checks
- *    this on the host before launching, so a bad pointer is an error code, not
- *    a GPU fault.
+ *    tensors, managed memory, or page-locked host memory from cudaHostAlloc /
+ *    cudaHostRegister).  The caller owns them.  Each must be 16-byte aligned
+ *    (AES_ERR_ALIGN) and [ptr, ptr + 16*nblocks) must lie inside one such
+ *    allocation (AES_ERR_ARG otherwise; unregistered pageable host memory is
+ *    refused because its extent cannot be checked).  The library checks this
+ *    on the host before launching, so a bad pointer is an error code, not a
+ *    GPU fault.
  *  - in == out (in place) is allowed unless a call says otherwise; any other
  *    overlap of the two ranges is rejected (AES_ERR_ARG).
  *  - nblocks == 0 returns AES_OK and launches nothing.

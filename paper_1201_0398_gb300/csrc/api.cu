@@ -90,9 +90,9 @@ static int expand(const uint8_t* key, int bits, uint32_t* enc, uint32_t* dec) {
 static std::mutex g_dev_mu;
 static DeviceInfo g_dev[64];
 static bool g_dev_ok[64];
-typedef CUresult (*GetRangeFn)(CUdeviceptr*, size_t*, CUdeviceptr);
-static GetRangeFn g_get_range = nullptr;
-static bool g_get_range_tried = false;
+typedef CUresult (*PointerAttrFn)(void*, CUpointer_attribute, CUdeviceptr);
+static PointerAttrFn g_ptr_attr = nullptr;
+static bool g_ptr_attr_tried = false;
 
 int current_device_info(DeviceInfo* info) {
     int dev = 0;
@@ -114,20 +114,24 @@ int current_device_info(DeviceInfo* info) {
     return AES_OK;
 }
 
-static GetRangeFn address_range_fn() {
+static PointerAttrFn pointer_attr_fn() {
     std::lock_guard<std::mutex> lk(g_dev_mu);
-    if (!g_get_range_tried) {
-        g_get_range_tried = true;
+    if (!g_ptr_attr_tried) {
+        g_ptr_attr_tried = true;
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &fn, 12000, cudaEnableDefault, &q) ==
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &fn, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            g_get_range = (GetRangeFn)fn;
+            g_ptr_attr = (PointerAttrFn)fn;
     }
-    return g_get_range;
+    return g_ptr_attr;
 }
 
+// Accepts device, managed and page-locked host memory whose allocation holds
+// all of [p, p+bytes); fails closed when the allocation's extent cannot be read.
+// Unregistered pageable host memory is refused even where the GPU could read
+// it, because its extent cannot be checked before the launch.
 int check_device_range(const void* p, size_t bytes, const char* what) {
     if (!p) return fail(AES_ERR_ARG, "%s is NULL", what);
     if (((uintptr_t)p & 15u) != 0) return fail(AES_ERR_ALIGN, "%s (%p) is not 16-byte aligned", what, p);
@@ -137,26 +141,20 @@ int check_device_range(const void* p, size_t bytes, const char* what) {
         cudaGetLastError();
         return fail(AES_ERR_ARG, "%s (%p): not a pointer CUDA knows: %s", what, p, cudaGetErrorString(e));
     }
-    if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) {
-        GetRangeFn range = address_range_fn();
-        if (range) {
-            CUdeviceptr b = 0;
-            size_t sz = 0;
-            if (range(&b, &sz, (CUdeviceptr)p) == CUDA_SUCCESS) {
-                const uintptr_t lo = (uintptr_t)p, end = (uintptr_t)b + sz;
-                if (bytes > end - lo)
-                    return fail(AES_ERR_ARG, "%s: %zu bytes at %p run past the end of its allocation (%zu bytes left)",
-                                what, bytes, p, (size_t)(end - lo));
-            }
-        }
-        return AES_OK;
-    }
-    if (attr.type == cudaMemoryTypeHost) return AES_OK;  // pinned / registered host memory, mapped for the GPU
-    DeviceInfo info;
-    int rc = current_device_info(&info);
-    if (rc) return rc;
-    if (info.pageable_access) return AES_OK;  // GPU reads pageable host memory (ATS)
-    return fail(AES_ERR_ARG, "%s (%p) is pageable host memory this GPU cannot read", what, p);
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged && attr.type != cudaMemoryTypeHost)
+        return fail(AES_ERR_ARG, "%s (%p) is not device, managed or page-locked host memory", what, p);
+    PointerAttrFn get = pointer_attr_fn();
+    if (!get) return fail(AES_ERR_CUDA, "cuPointerGetAttribute unavailable: cannot check the extent of %s", what);
+    CUdeviceptr start = 0;
+    size_t size = 0;
+    if (get(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, (CUdeviceptr)p) != CUDA_SUCCESS ||
+        get(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, (CUdeviceptr)p) != CUDA_SUCCESS)
+        return fail(AES_ERR_ARG, "%s (%p): the extent of its allocation cannot be read", what, p);
+    const uintptr_t lo = (uintptr_t)p, end = (uintptr_t)start + size;
+    if (lo < (uintptr_t)start || lo > end || bytes > end - lo)
+        return fail(AES_ERR_ARG, "%s: %zu bytes at %p run past the end of its allocation (%zu bytes left)", what,
+                    bytes, p, lo <= end ? (size_t)(end - lo) : (size_t)0);
+    return AES_OK;
 }
 
 // ------------------------------------------------------- launch defaults
