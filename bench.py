@@ -17,6 +17,12 @@ six launches, 6 GiB of plaintext-equivalent bytes per step and GPU.  The buffers
             all inside the timed region.
   cpu_baseline  the CPU oracle (plain byte-oriented AES) on all host cores on a
             bounded 64 MiB sample of each of the six operations (rank 0, N=1 only).
+  batched   10,000 messages (log-uniform 16 B - 4 MiB, own key each, key sizes
+            2:1:1, mixed directions) in one persistent launch, against the same
+            messages issued as 10,000 single-message launches.
+
+Launch shapes of the table kernel are chosen by the autotuner during setup
+(untimed) and reported under "tuned_shapes".
 
 --impl reference times the CPU oracle as the reference arm (rank 0 only).
 """
@@ -54,6 +60,9 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=0, help="0 = max(3, steps // 20)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--kernel", choices=("table", "bitsliced"), default="table")
+    p.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched (10,000-message) section")
+    p.add_argument("--batch-steps", type=int, default=10)
     return p.parse_args()
 
 
@@ -68,7 +77,7 @@ def measured_peaks():
 def kernel_fingerprint() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1201_0398_gb300", "csrc")
-    for name in ("ecb_table.cu", "aes_tables.h", "gbaes_internal.h"):
+    for name in ("ecb_table.cu", "aes_rounds.cuh", "aes_tables.h", "gbaes_internal.h"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -260,6 +269,11 @@ def run_ours(args):
         c[bits] = torch.empty_like(x[bits])
         p[bits] = torch.empty_like(x[bits])
     ops = [(bits, dec) for bits in BITS for dec in (False, True)]
+    tuned = {}
+    if kernel == g.KERNEL_TABLE and not args.no_tune:
+        from paper_1201_0398_gb300 import autotune
+
+        tuned = autotune.tune_all_ecb(nbytes=min(size, 256 * MiB))
 
     def launch(bits, dec):
         src, dst = (c[bits], p[bits]) if dec else (x[bits], c[bits])
@@ -310,7 +324,8 @@ def run_ours(args):
     dom_name, dom = max(op_stats.items(), key=lambda kv: kv[1]["ms"])
     bits_dom = int(dom_name[3:6])
     dec_dom = dom_name.endswith("dec")
-    ktpl = f"table_kernel<{NR[bits_dom]},{1 if dec_dom else 0},2>"
+    bpt_dom = tuned.get(dom_name, {}).get("blocks_per_thread", 2)
+    ktpl = f"table_kernel<{NR[bits_dom]},{1 if dec_dom else 0},{bpt_dom}>"
     traffic = dram_traffic(ktpl) if kernel == g.KERNEL_TABLE else None
     clock_frac = None
     if clk.get("sm_mhz"):
@@ -362,6 +377,13 @@ def run_ours(args):
            "path": "pinned host -> device copy, C-ABI ECB launch, device -> pinned host copy, serial on one stream"}
     del xh, ch, ph, dbuf_in, dbuf_out
 
+    batched = None
+    if not args.no_batched:
+        for t in (x, c, p):
+            t.clear()
+        torch.cuda.empty_cache()
+        batched = bench_batched(g, args, stream, world, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = 64 * MiB
@@ -381,12 +403,70 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (1 GiB > 129 MB), no flush",
                        "parallelism": f"replicas x{world} (independent buffers per rank)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(ops) * args.steps,
-            "clocks": clk, "ops": op_stats,
+            "clocks": clk, "ops": op_stats, "tuned_shapes": {k: f"{v['threads']}x{v['blocks_per_thread']}"
+                                                             for k, v in tuned.items()},
+            "batched": batched,
         }), flush=True)
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def bench_batched(g, args, stream, world, rank):
+    """10,000 messages (log-uniform 16 B - 4 MiB, own key each, key sizes 2:1:1,
+    mixed directions) in one persistent launch; compared with the same messages
+    issued as 10,000 single-message launches."""
+    import numpy as np
+    import torch
+
+    from paper_1201_0398_gb300 import autotune, workloads
+
+    w = workloads.batch_workload(seed=workloads.SEED_BATCH + 97 * rank)
+    keys = [g.Key(k) for k in w.keys]
+    nblocks = w.lengths // 16
+    off = np.concatenate([[0], np.cumsum(w.lengths)[:-1]])
+    descs = g.make_descs(off, off, nblocks, np.arange(len(keys)), w.decrypt)
+    x = workloads.device_bytes(workloads.SEED_BATCH + 97 * rank, w.total_bytes, device=torch.device("cuda"))
+    y = torch.empty_like(x)
+    plan, report = autotune.tune_batch(descs, keys, x, y)
+    plan.launch(x, y, stream=stream)
+    alone = torch.empty_like(x)
+    for i in range(len(keys)):
+        a, n = int(off[i]), int(w.lengths[i])
+        g.ecb_ex(keys[i], x[a:a + n], alone[a:a + n], decrypt=bool(w.decrypt[i]), stream=stream)
+    torch.cuda.synchronize()
+    if not torch.equal(alone, y):
+        raise RuntimeError("batched output differs from the single-message kernel")
+
+    def timed(fn, reps):
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(world, e0.elapsed_time(e1) / 1e3 / reps)
+
+    reps = max(3, args.batch_steps)
+    t_plan = timed(lambda: plan.launch(x, y, stream=stream), reps)
+    t_graph = timed(lambda: plan.launch(x, y, stream=stream, graph=True), reps)
+
+    def single_loop():
+        for i in range(len(keys)):
+            a, n = int(off[i]), int(w.lengths[i])
+            g.ecb_ex(keys[i], x[a:a + n], alone[a:a + n], decrypt=bool(w.decrypt[i]), stream=stream)
+
+    t_loop = timed(single_loop, 2)
+    total = w.total_bytes
+    return {"value": world * total / t_plan / 1e9, "unit": "GB/s", "messages": len(keys), "bytes": total,
+            "ms": 1e3 * t_plan, "graph_gbs": world * total / t_graph / 1e9,
+            "single_launch_loop_gbs": world * total / t_loop / 1e9, "shape": report["best"],
+            "candidates_ms": report["candidates_ms"], "launches_per_step": 1,
+            "workload": "10,000 messages, log-uniform 16 B-4 MiB (x16 B), keys 128/192/256 at 2:1:1, "
+                        "encrypt/decrypt 50/50, one persistent launch"}
 
 
 def main():

@@ -114,6 +114,60 @@ int aes_ctr_xcrypt(const aes_ctx* ctx, const uint8_t* iv, int counter_kind, uint
  * overlap at all (each output depends on two input blocks). */
 int aes_cbc_decrypt(const aes_ctx* ctx, const uint8_t* iv, const void* in, void* out, size_t nblocks, void* stream);
 
+/* ---------------------------------------------------------------- batched
+ * Many messages, each with its own key, key size and direction, in ONE
+ * persistent launch (pattern: batching).  The paper issues one draw per
+ * buffer and notes that per-operation overhead dominates small inputs
+ * (Section 3.1; Section 4 advises against small messages); batching amortises
+ * that overhead over thousands of messages.  Messages may be in-place
+ * (in_base+in_off == out_base+out_off); otherwise outputs must not overlap
+ * any other message's input or output (not checked). */
+typedef struct aes_msg_desc {
+    uint64_t in_off;    /* byte offset of the message's input from in_base (multiple of 16) */
+    uint64_t out_off;   /* byte offset of its output from out_base (multiple of 16) */
+    uint64_t nblocks;   /* 16-byte blocks (0 = nothing to do) */
+    uint32_t key_index; /* index into the ctxs array */
+    uint32_t decrypt;   /* 0 = encrypt, 1 = decrypt */
+} aes_msg_desc;
+
+typedef struct aes_batch_plan aes_batch_plan;
+
+/* Builds a reusable plan: validates every descriptor (AES_ERR_ARG /
+ * AES_ERR_ALIGN), groups messages by direction and key size, tiles the
+ * flattened blocks (threads * blocks_per_thread blocks per tile; 0, 0 =
+ * 1024, 2) and uploads the tile table, message table and every context's two
+ * schedules to one device allocation on the current device (cudaMalloc,
+ * synchronous).  msgs and ctxs are HOST arrays, read during the call only.
+ * Returns NULL on error. */
+aes_batch_plan* aes_batch_plan_create(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx,
+                                      int threads, int blocks_per_thread);
+
+/* Launches a plan on `stream`: resets the plan's tile counter, then one
+ * persistent kernel (one CTA per SM).  in_base/out_base: device buffers of
+ * in_bytes/out_bytes bytes that must cover every message (AES_ERR_ARG).  Two
+ * launches of the same plan must not run concurrently (they share its tile
+ * counter); stream-ordered repeats are fine. */
+int aes_batch_plan_launch(aes_batch_plan* plan, const void* in_base, size_t in_bytes, void* out_base,
+                          size_t out_bytes, void* stream);
+
+/* Same as aes_batch_plan_launch through a CUDA graph captured on first use
+ * (counter reset + kernel) and replayed afterwards; new base pointers update
+ * the captured kernel's arguments.  Same concurrency rule. */
+int aes_batch_plan_launch_graph(aes_batch_plan* plan, const void* in_base, size_t in_bytes, void* out_base,
+                                size_t out_bytes, void* stream);
+
+/* Plan statistics (any output may be NULL). */
+int aes_batch_plan_info(const aes_batch_plan* plan, uint64_t* total_blocks, uint32_t* ntiles, uint32_t* tile_blocks);
+
+/* Frees a plan (synchronises with the device through cudaFree). */
+void aes_batch_plan_free(aes_batch_plan* plan);
+
+/* One-shot batch: plan tables in stream-ordered scratch (cudaMallocAsync /
+ * cudaFreeAsync on `stream`), one launch with 1024 threads x 2 blocks per
+ * tile.  Same arguments and rules as the plan calls. */
+int aes_ecb_batch(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx, const void* in_base,
+                  size_t in_bytes, void* out_base, size_t out_bytes, void* stream);
+
 /* Default kernel variant for aes_encrypt_ecb / aes_decrypt_ecb (process-wide;
  * AES_KERNEL_TABLE at start).  Returns the previous variant or AES_ERR_ARG. */
 int aes_set_kernel(int which);
@@ -143,6 +197,15 @@ int aes_key_schedule(const uint8_t* key, int bits, uint32_t* enc_rk, uint32_t* d
  * T_k = rotl(T_0, 8k)), the S-box and the inverse S-box (256 bytes each).  Any
  * pointer may be NULL.  Returns AES_OK. */
 int aes_host_tables(uint32_t* te0, uint32_t* td0, uint8_t* sbox, uint8_t* inv_sbox);
+
+/* Host-only view of a batch's tiling: validates the descriptors like
+ * aes_batch_plan_create and writes, for each tile of tile_blocks blocks, the
+ * caller's index of the first message that tile touches (tiles in plan order:
+ * encryption groups 128/192/256, then decryption groups).  first_msg may be
+ * NULL; otherwise it holds cap entries.  Returns the number of tiles or a
+ * negative code.  Needs no GPU. */
+int aes_batch_tiles(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx, int tile_blocks,
+                    uint32_t* first_msg, size_t cap);
 
 #ifdef __cplusplus
 }

@@ -31,6 +31,11 @@ __all__ = [
     "device_status",
     "key_schedule",
     "host_tables",
+    "MSG_DESC",
+    "make_descs",
+    "BatchPlan",
+    "ecb_batch",
+    "batch_tiles",
     "KERNEL_TABLE",
     "KERNEL_BITSLICED",
     "CTR_BE128",
@@ -88,6 +93,13 @@ def _declare(lib):
         "aes_last_error": (c.c_char_p, []),
         "aes_key_schedule": (c.c_int, [u8p, c.c_int, u32p, u32p]),
         "aes_host_tables": (c.c_int, [u32p, u32p, u8p, u8p]),
+        "aes_batch_plan_create": (vp, [vp, sz, vp, sz, c.c_int, c.c_int]),
+        "aes_batch_plan_launch": (c.c_int, [vp, vp, sz, vp, sz, vp]),
+        "aes_batch_plan_launch_graph": (c.c_int, [vp, vp, sz, vp, sz, vp]),
+        "aes_batch_plan_info": (c.c_int, [vp, c.POINTER(c.c_uint64), u32p, u32p]),
+        "aes_batch_plan_free": (None, [vp]),
+        "aes_ecb_batch": (c.c_int, [vp, sz, vp, sz, vp, sz, vp, sz, vp]),
+        "aes_batch_tiles": (c.c_int, [vp, sz, vp, sz, c.c_int, u32p, sz]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -266,3 +278,84 @@ def host_tables():
     u32 = ctypes.POINTER(ctypes.c_uint32)
     _check(load().aes_host_tables(te0.ctypes.data_as(u32), td0.ctypes.data_as(u32), _u8p(s), _u8p(si)))
     return te0, td0, s, si
+
+
+# ------------------------------------------------------------------- batched
+
+# Matches struct aes_msg_desc (32 bytes).
+MSG_DESC = np.dtype([("in_off", "<u8"), ("out_off", "<u8"), ("nblocks", "<u8"), ("key_index", "<u4"),
+                     ("decrypt", "<u4")])
+
+
+def make_descs(in_off, out_off, nblocks, key_index, decrypt) -> np.ndarray:
+    """Array of aes_msg_desc from per-message sequences (byte offsets, blocks, key index, direction)."""
+    n = len(nblocks)
+    d = np.zeros(n, MSG_DESC)
+    d["in_off"] = np.asarray(in_off, np.uint64)
+    d["out_off"] = np.asarray(out_off, np.uint64)
+    d["nblocks"] = np.asarray(nblocks, np.uint64)
+    d["key_index"] = np.asarray(key_index, np.uint32)
+    d["decrypt"] = np.asarray(decrypt, np.uint32)
+    return d
+
+
+def _ctx_array(keys):
+    arr = (ctypes.c_void_p * max(1, len(keys)))(*[k.handle.value for k in keys])
+    return arr
+
+
+class BatchPlan:
+    """A reusable batched launch (aes_batch_plan): descriptors + key contexts."""
+
+    def __init__(self, descs: np.ndarray, keys, threads: int = 0, blocks_per_thread: int = 0):
+        descs = np.ascontiguousarray(descs, MSG_DESC)
+        self._lib = load()
+        self._keys = list(keys)  # keep the contexts alive
+        ctxs = _ctx_array(self._keys)
+        h = self._lib.aes_batch_plan_create(ctypes.c_void_p(descs.ctypes.data), descs.size, ctxs, len(self._keys),
+                                            int(threads), int(blocks_per_thread))
+        if not h:
+            _check(-1)
+        self._h = ctypes.c_void_p(h)
+
+    def info(self):
+        tb = ctypes.c_uint64()
+        nt = ctypes.c_uint32()
+        tbl = ctypes.c_uint32()
+        _check(self._lib.aes_batch_plan_info(self._h, ctypes.byref(tb), ctypes.byref(nt), ctypes.byref(tbl)))
+        return {"total_blocks": tb.value, "ntiles": nt.value, "tile_blocks": tbl.value}
+
+    def launch(self, inp, out, stream=None, graph: bool = False):
+        fn = self._lib.aes_batch_plan_launch_graph if graph else self._lib.aes_batch_plan_launch
+        _check(fn(self._h, _ptr(inp), inp.numel() * inp.element_size(), _ptr(out), out.numel() * out.element_size(),
+                  _stream_handle(stream)))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.aes_batch_plan_free(h)
+            self._h = None
+
+
+def ecb_batch(descs: np.ndarray, keys, inp, out, stream=None):
+    """One-shot batched launch (stream-ordered scratch for the plan tables)."""
+    descs = np.ascontiguousarray(descs, MSG_DESC)
+    ctxs = _ctx_array(list(keys))
+    _check(load().aes_ecb_batch(ctypes.c_void_p(descs.ctypes.data), descs.size, ctxs, len(keys), _ptr(inp),
+                                inp.numel() * inp.element_size(), _ptr(out), out.numel() * out.element_size(),
+                                _stream_handle(stream)))
+    return out
+
+
+def batch_tiles(descs: np.ndarray, keys, tile_blocks: int) -> np.ndarray:
+    """Host-only tiling of a batch: caller's index of each tile's first message."""
+    descs = np.ascontiguousarray(descs, MSG_DESC)
+    ctxs = _ctx_array(list(keys))
+    lib = load()
+    n = _check(lib.aes_batch_tiles(ctypes.c_void_p(descs.ctypes.data), descs.size, ctxs, len(keys), int(tile_blocks),
+                                   None, 0))
+    out = np.zeros(max(n, 1), np.uint32)
+    _check(lib.aes_batch_tiles(ctypes.c_void_p(descs.ctypes.data), descs.size, ctxs, len(keys), int(tile_blocks),
+                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), out.size))
+    return out[:n]

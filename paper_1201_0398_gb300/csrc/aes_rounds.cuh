@@ -1,0 +1,213 @@
+// Device-side AES rounds in the T-table form of Eq. 1, shared by the block
+// kernels (ecb_table.cu) and the batched kernel (batch.cu).
+//
+// Shared-memory layout (bank-conflict free, one PRMT per lookup address):
+//   * Every table is replicated 32 times; lane l reads copy l, so lane l always
+//     hits bank l whatever byte it looks up.
+//   * Region r (64 KiB) holds T_{2r} and T_{2r+1}: word 64*x + 32*slot + l is
+//     T_{2r+slot}[x] for lane l, i.e. byte address x<<8 | slot<<7 | l<<2.  A
+//     __byte_perm drops state byte k into address byte 1 beside a per-lane
+//     constant (l<<2 | slot<<7 | the region base, which is 64 KiB aligned).
+//     Region 1 is reached through the load's immediate offset.
+//   * The inverse cipher adds the inverse S-box for its last round (32x
+//     replicated, 32 words per entry) after the two regions.
+// T_k[x] = rotl(T_0[x], 8k) (Eq. 1's four tables are rotations of one).
+#pragma once
+
+#include <cstdint>
+
+#include "aes_tables.h"
+#include "gbaes_internal.h"
+
+namespace gbaes {
+
+static __constant__ AesTables c_tab = make_aes_tables();
+
+constexpr uint32_t kRegion = 0x10000u;                 // one 64 KiB region: two tables
+constexpr uint32_t kEncBytes = 2 * kRegion;            // T0|T1, T2|T3
+constexpr uint32_t kSiOffset = 2 * kRegion;            // inverse cipher: inverse S-box
+constexpr uint32_t kDecBytes = 2 * kRegion + 0x8000u;  // + 256 entries x 32 lanes x 4 B
+
+__device__ __forceinline__ uint32_t lds(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+template <uint32_t OFF>
+__device__ __forceinline__ uint32_t lds_off(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.b32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
+    return v;
+}
+
+__device__ __forceinline__ void sts(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t smem_base(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t dynamic_smem_bytes() {
+    uint32_t dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    return dyn;
+}
+
+// 64 KiB-aligned start of the table layout inside the dynamic window.
+__device__ __forceinline__ uint32_t table_base(uint32_t base) { return (base + (kRegion - 1)) & ~(kRegion - 1); }
+
+// Writes the tables of one direction into shared memory at A (all threads of
+// the CTA take part; the caller synchronises afterwards).
+__device__ __forceinline__ void fill_tables(uint32_t A, bool decrypt) {
+    const uint32_t* t0 = decrypt ? c_tab.td0 : c_tab.te0;
+    // Region r, slot s, entry x, lane l at word 64x + 32s + l = rotl(T0[x], 8(2r+s)).
+    for (uint32_t w = threadIdx.x; w < (kEncBytes >> 2); w += blockDim.x) {
+        const uint32_t x = (w >> 6) & 255u;
+        const uint32_t rot = 8u * (2u * (w >> 14) + ((w >> 5) & 1u));
+        const uint32_t v = t0[x];
+        sts(A + 4u * w, __funnelshift_l(v, v, rot));
+    }
+    if (decrypt) {
+        for (uint32_t w = threadIdx.x; w < 8192u; w += blockDim.x) sts(A + kSiOffset + 4u * w, c_tab.si4[w >> 5]);
+    }
+}
+
+// Address of T_{2*region+slot}[byte K of w] for this lane (region offset aside):
+// byte 0 <- lane constant (l<<2 | slot<<7), byte 1 <- byte K of w, bytes 2,3 <-
+// the 64 KiB-aligned base carried in the lane constant.
+template <int K>
+__device__ __forceinline__ uint32_t taddr(uint32_t w, uint32_t lane_const) {
+    return __byte_perm(w, lane_const, 0x7604u | (K << 4));
+}
+
+// (a & m) | (b & ~m): bytes of a where m is set, of b elsewhere.
+__device__ __forceinline__ uint32_t merge(uint32_t a, uint32_t b, uint32_t m) { return (a & m) | (b & ~m); }
+
+// One inner encryption round (Eq. 1).
+__device__ __forceinline__ void enc_round(uint32_t (&s)[4], uint32_t L0, uint32_t L1, uint4 k) {
+    uint32_t t[4];
+    const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t a0 = lds(taddr<0>(s[j], L0));                         // T0[I_{j,0}]
+        uint32_t a1 = lds(taddr<1>(s[(j + 1) & 3], L1));               // T1[I_{j+1,1}]
+        uint32_t a2 = lds_off<kRegion>(taddr<2>(s[(j + 2) & 3], L0));  // T2[I_{j+2,2}]
+        uint32_t a3 = lds_off<kRegion>(taddr<3>(s[(j + 3) & 3], L1));  // T3[I_{j+3,3}]
+        t[j] = a0 ^ a1 ^ a2 ^ a3 ^ kk[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = t[j];
+}
+
+// Last encryption round: SubBytes + ShiftRows + AddRoundKey.  S[x] is a byte of
+// each rotated table: byte 0 of T2, byte 1 of T3, byte 2 of T0, byte 3 of T1.
+__device__ __forceinline__ void enc_last(uint32_t (&s)[4], uint32_t L0, uint32_t L1, uint4 k) {
+    uint32_t t[4];
+    const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t e0 = lds_off<kRegion>(taddr<0>(s[j], L0));            // T2: byte 0 = S
+        uint32_t e1 = lds_off<kRegion>(taddr<1>(s[(j + 1) & 3], L1));  // T3: byte 1 = S
+        uint32_t e2 = lds(taddr<2>(s[(j + 2) & 3], L0));               // T0: byte 2 = S
+        uint32_t e3 = lds(taddr<3>(s[(j + 3) & 3], L1));               // T1: byte 3 = S
+        uint32_t o = merge(e0, e1, 0x000000ffu);
+        o = merge(o, e2, 0x0000ffffu);
+        o = merge(o, e3, 0x00ffffffu);
+        t[j] = o ^ kk[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = t[j];
+}
+
+// One inner round of the equivalent inverse cipher: Td tables, I_{j-k,k}.
+__device__ __forceinline__ void dec_round(uint32_t (&s)[4], uint32_t L0, uint32_t L1, uint4 k) {
+    uint32_t t[4];
+    const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t a0 = lds(taddr<0>(s[j], L0));                         // Td0[I_{j,0}]
+        uint32_t a1 = lds(taddr<1>(s[(j + 3) & 3], L1));               // Td1[I_{j-1,1}]
+        uint32_t a2 = lds_off<kRegion>(taddr<2>(s[(j + 2) & 3], L0));  // Td2[I_{j-2,2}]
+        uint32_t a3 = lds_off<kRegion>(taddr<3>(s[(j + 1) & 3], L1));  // Td3[I_{j-3,3}]
+        t[j] = a0 ^ a1 ^ a2 ^ a3 ^ kk[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = t[j];
+}
+
+// Inverse S-box entry for byte K of w: 32x replicated table, 32 words per entry.
+template <int K>
+__device__ __forceinline__ uint32_t si_lookup(uint32_t w, uint32_t L0) {
+    uint32_t b = (w >> (8 * K)) & 0xffu;
+    return lds_off<kSiOffset>((b << 7) | L0);
+}
+
+// Last round of the inverse cipher: InvShiftRows + InvSubBytes + AddRoundKey.
+__device__ __forceinline__ void dec_last(uint32_t (&s)[4], uint32_t L0, uint4 k) {
+    uint32_t t[4];
+    const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t d0 = si_lookup<0>(s[j], L0);
+        uint32_t d1 = si_lookup<1>(s[(j + 3) & 3], L0);
+        uint32_t d2 = si_lookup<2>(s[(j + 2) & 3], L0);
+        uint32_t d3 = si_lookup<3>(s[(j + 1) & 3], L0);
+        uint32_t o = merge(d0, d1, 0x000000ffu);
+        o = merge(o, d2, 0x0000ffffu);
+        o = merge(o, d3, 0x00ffffffu);
+        t[j] = o ^ kk[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = t[j];
+}
+
+// Round keys from the kernel parameters (uniform constant-bank operands).
+struct ParamKeys {
+    const uint32_t (&rk)[60];
+    __device__ __forceinline__ uint4 get(int r) const {
+        return make_uint4(rk[4 * r], rk[4 * r + 1], rk[4 * r + 2], rk[4 * r + 3]);
+    }
+};
+
+// Round keys from a schedule in global memory (read-only path; 16 B per round).
+struct GlobalKeys {
+    const uint4* p;
+    __device__ __forceinline__ uint4 get(int r) const { return __ldg(p + r); }
+};
+
+// Full cipher on BPT independent states sharing one schedule, rounds
+// interleaved across the states.
+template <int NR, bool DECRYPT, int BPT, class KS>
+__device__ __forceinline__ void cipher(uint32_t (&s)[BPT][4], const KS& ks, uint32_t L0, uint32_t L1) {
+    {
+        const uint4 k = ks.get(0);
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            s[b][0] ^= k.x;
+            s[b][1] ^= k.y;
+            s[b][2] ^= k.z;
+            s[b][3] ^= k.w;
+        }
+    }
+#pragma unroll
+    for (int r = 1; r < NR; ++r) {
+        const uint4 k = ks.get(r);
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            if (DECRYPT)
+                dec_round(s[b], L0, L1, k);
+            else
+                enc_round(s[b], L0, L1, k);
+        }
+    }
+    const uint4 k = ks.get(NR);
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        if (DECRYPT)
+            dec_last(s[b], L0, k);
+        else
+            enc_last(s[b], L0, L1, k);
+    }
+}
+
+}  // namespace gbaes

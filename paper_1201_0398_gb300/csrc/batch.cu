@@ -1,0 +1,590 @@
+// Batched multi-key AES-ECB: many messages, each with its own key, key size and
+// direction, in one persistent launch.
+//
+// The paper's draw-per-buffer design pays a per-operation overhead that
+// dominates small inputs (Section 3.1; its conclusion advises against small
+// messages).  Here thousands of messages share one launch:
+//
+//  * Host plan.  Messages are grouped by (direction, key size) -- encryption
+//    groups first -- and each group's blocks are numbered contiguously.  The
+//    flattened block space is cut into tiles of threads*BPT blocks; for every
+//    tile the plan records the first message it touches.  Each (key, direction)
+//    gets a slot holding its 4*(Nr+1)-word schedule.  Everything sits in one
+//    device buffer, uploaded once per plan.
+//  * Kernel.  One CTA per SM pulls tile indices from a global atomic counter.
+//    Because encryption tiles come first, a CTA rebuilds its shared-memory
+//    tables (aes_rounds.cuh) at most once, when it first meets a decryption
+//    tile.  Within a tile each block finds its message by binary search over
+//    the tile's message range (no search when the tile lies in one message),
+//    and the rounds read the message's round keys from global memory (L1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "aes_rounds.cuh"
+
+namespace gbaes {
+
+struct MsgDev {  // 32 bytes, group order
+    uint64_t blk_start;  // first block of the message in its group's block space
+    uint64_t in_blk;     // in_off / 16
+    uint64_t out_blk;    // out_off / 16
+    uint32_t key_slot;   // schedule slot (2 * key_index + decrypt)
+    uint32_t src;        // caller's message index
+};
+
+struct GroupDev {
+    uint32_t tile_start, tile_end;  // tiles [tile_start, tile_end)
+    uint32_t msg_start, msg_end;    // messages [msg_start, msg_end) in group order
+    uint64_t blocks;                // blocks in the group
+    int32_t nr;
+    int32_t dir;  // 0 encrypt, 1 decrypt
+};
+
+constexpr int kGroups = 6;
+constexpr int kSlotWords = 64;  // 60 used (Nr = 14), padded to 256 bytes
+
+struct BatchArgs {
+    const uint4* in;
+    uint4* out;
+    const MsgDev* msgs;
+    const uint4* keys;  // kSlotWords / 4 uint4 per slot
+    const uint32_t* tile_msg;
+    unsigned* counter;
+    int* status;
+    uint32_t ntiles;
+    uint32_t tile_blocks;
+    GroupDev groups[kGroups];
+};
+
+template <int NR, bool DEC, int BPT>
+__device__ __forceinline__ void batch_tile(const BatchArgs& a, const GroupDev& G, uint32_t t, uint32_t L0,
+                                           uint32_t L1) {
+    const uint64_t gb0 = (uint64_t)(t - G.tile_start) * a.tile_blocks;
+    const uint32_t m_lo = a.tile_msg[t];
+    const uint32_t m_hi = (t + 1 < G.tile_end) ? a.tile_msg[t + 1] : G.msg_end - 1;
+    uint32_t s[BPT][4];
+    uint64_t oidx[BPT];
+    const uint4* kp[BPT];
+    bool ok[BPT];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const uint64_t gb = gb0 + threadIdx.x + (uint64_t)b * blockDim.x;
+        ok[b] = gb < G.blocks;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        kp[b] = nullptr;
+        oidx[b] = 0;
+        if (ok[b]) {
+            uint32_t m = m_lo;
+            if (m_hi != m_lo) {  // largest m in [m_lo, m_hi] with blk_start[m] <= gb
+                uint32_t lo = m_lo, hi = m_hi;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (__ldg((const unsigned long long*)(a.msgs + mid)) <= gb)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                m = lo;
+            }
+            const uint4* mp = (const uint4*)(a.msgs + m);
+            const uint4 q0 = __ldg(mp), q1 = __ldg(mp + 1);
+            const uint64_t blk_start = ((uint64_t)q0.y << 32) | q0.x;
+            const uint64_t in_blk = ((uint64_t)q0.w << 32) | q0.z;
+            const uint64_t out_blk = ((uint64_t)q1.y << 32) | q1.x;
+            const uint64_t off = gb - blk_start;
+            v = __ldcs(a.in + in_blk + off);
+            oidx[b] = out_blk + off;
+            kp[b] = a.keys + (uint64_t)q1.z * (kSlotWords / 4);
+        }
+        s[b][0] = v.x;
+        s[b][1] = v.y;
+        s[b][2] = v.z;
+        s[b][3] = v.w;
+    }
+    if (!ok[0]) return;  // blocks of a thread are in increasing order: none valid
+    bool same = true;
+#pragma unroll
+    for (int b = 1; b < BPT; ++b) same = same && (!ok[b] || kp[b] == kp[0]);
+    if (same) {
+        cipher<NR, DEC, BPT>(s, GlobalKeys{kp[0]}, L0, L1);
+    } else {
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            if (ok[b]) cipher<NR, DEC, 1>(*reinterpret_cast<uint32_t(*)[1][4]>(&s[b]), GlobalKeys{kp[b]}, L0, L1);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < BPT; ++b)
+        if (ok[b]) __stcs(a.out + oidx[b], make_uint4(s[b][0], s[b][1], s[b][2], s[b][3]));
+}
+
+// Group table staged in shared memory (read with a runtime index each tile).
+__device__ __forceinline__ GroupDev load_group(uint32_t gaddr, int g) {
+    GroupDev G;
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w[i] = lds(gaddr + 32u * g + 4u * i);
+    G.tile_start = w[0];
+    G.tile_end = w[1];
+    G.msg_start = w[2];
+    G.msg_end = w[3];
+    G.blocks = ((uint64_t)w[5] << 32) | w[4];
+    G.nr = (int32_t)w[6];
+    G.dir = (int32_t)w[7];
+    return G;
+}
+
+template <int BPT>
+__global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const uint32_t base = smem_base(smem_raw);
+    const uint32_t A = table_base(base);
+    const uint32_t slot = (base + dynamic_smem_bytes() - 16u) & ~15u;  // tile-index broadcast word
+    const uint32_t gaddr = slot - 32u * kGroups;                        // group table
+    if (A + kDecBytes > gaddr) {
+        if (threadIdx.x == 0) atomicOr(a.status, 2);
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < kGroups; ++i) {
+        if (threadIdx.x == (unsigned)i) {
+            const GroupDev& G = a.groups[i];
+            const uint32_t w[8] = {G.tile_start, G.tile_end, G.msg_start, G.msg_end, (uint32_t)G.blocks,
+                                   (uint32_t)(G.blocks >> 32), (uint32_t)G.nr, (uint32_t)G.dir};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sts(gaddr + 32u * i + 4u * k, w[k]);
+        }
+    }
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t L0 = A | (lane << 2);
+    const uint32_t L1 = L0 | 128u;
+    int cur_dir = -1;
+    for (;;) {
+        if (threadIdx.x == 0) sts(slot, atomicAdd(a.counter, 1u));
+        __syncthreads();
+        const uint32_t t = lds(slot);
+        __syncthreads();
+        if (t >= a.ntiles) break;
+        int g = 0;
+        while (g < kGroups - 1 && t >= lds(gaddr + 32u * g + 4u)) ++g;  // tile_end of group g
+        const GroupDev G = load_group(gaddr, g);
+        if (G.dir != cur_dir) {  // CTA-uniform: every thread saw the same t
+            fill_tables(A, G.dir != 0);
+            __syncthreads();
+            cur_dir = G.dir;
+        }
+        switch (G.nr * 2 + G.dir) {
+            case 20: batch_tile<10, false, BPT>(a, G, t, L0, L1); break;
+            case 21: batch_tile<10, true, BPT>(a, G, t, L0, L1); break;
+            case 24: batch_tile<12, false, BPT>(a, G, t, L0, L1); break;
+            case 25: batch_tile<12, true, BPT>(a, G, t, L0, L1); break;
+            case 28: batch_tile<14, false, BPT>(a, G, t, L0, L1); break;
+            case 29: batch_tile<14, true, BPT>(a, G, t, L0, L1); break;
+            default: break;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host plan
+
+struct HostPlan {
+    std::vector<MsgDev> msgs;
+    std::vector<uint32_t> tile_msg;
+    std::vector<uint32_t> keys;  // 2 * nctx slots of kSlotWords words
+    GroupDev groups[kGroups];
+    uint32_t ntiles = 0;
+    uint32_t tile_blocks = 0;
+    uint64_t total_blocks = 0;
+    uint64_t in_extent = 0;   // bytes from in_base the plan reads
+    uint64_t out_extent = 0;  // bytes from out_base the plan writes
+};
+
+static int group_of(int nr, int dir) { return dir * 3 + (nr == 10 ? 0 : nr == 12 ? 1 : 2); }
+
+// Validates the descriptors and lays out groups, tiles and key slots.
+static int build_host_plan(const aes_msg_desc* d, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx,
+                           uint32_t tile_blocks, bool with_keys, HostPlan* P) {
+    if (nmsg && !d) return fail(AES_ERR_ARG, "message descriptors are NULL");
+    if (nctx && !ctxs) return fail(AES_ERR_ARG, "key contexts are NULL");
+    if (nmsg > 0xFFFFFFF0u) return fail(AES_ERR_ARG, "too many messages (%zu)", nmsg);
+    if (tile_blocks == 0) return fail(AES_ERR_ARG, "tile size is zero");
+    for (size_t i = 0; i < nctx; ++i)
+        if (!ctxs[i] || ctxs[i]->magic != kCtxMagic) return fail(AES_ERR_ARG, "ctxs[%zu] is not a valid aes_ctx", i);
+    std::vector<uint32_t> order[kGroups];
+    for (size_t i = 0; i < nmsg; ++i) {
+        const aes_msg_desc& m = d[i];
+        if (m.key_index >= nctx) return fail(AES_ERR_ARG, "message %zu: key_index %u >= %zu", i, m.key_index, nctx);
+        if (m.decrypt > 1) return fail(AES_ERR_ARG, "message %zu: decrypt must be 0 or 1", i);
+        if ((m.in_off | m.out_off) & 15u) return fail(AES_ERR_ALIGN, "message %zu: offsets must be multiples of 16", i);
+        if (m.nblocks > (UINT64_MAX >> 5)) return fail(AES_ERR_ARG, "message %zu: nblocks too large", i);
+        const uint64_t bytes = m.nblocks * 16;
+        if (m.in_off > UINT64_MAX - bytes || m.out_off > UINT64_MAX - bytes)
+            return fail(AES_ERR_ARG, "message %zu: offset + length overflows", i);
+        if (m.nblocks == 0) continue;
+        P->in_extent = std::max<uint64_t>(P->in_extent, m.in_off + bytes);
+        P->out_extent = std::max<uint64_t>(P->out_extent, m.out_off + bytes);
+        order[group_of(ctxs[m.key_index]->nr, (int)m.decrypt)].push_back((uint32_t)i);
+    }
+    P->tile_blocks = tile_blocks;
+    uint64_t tiles = 0;
+    for (int g = 0; g < kGroups; ++g) {
+        GroupDev& G = P->groups[g];
+        G.nr = g % 3 == 0 ? 10 : g % 3 == 1 ? 12 : 14;
+        G.dir = g / 3;
+        G.msg_start = (uint32_t)P->msgs.size();
+        uint64_t blk = 0;
+        for (uint32_t i : order[g]) {
+            const aes_msg_desc& m = d[i];
+            MsgDev md;
+            md.blk_start = blk;
+            md.in_blk = m.in_off >> 4;
+            md.out_blk = m.out_off >> 4;
+            md.key_slot = 2u * m.key_index + m.decrypt;
+            md.src = i;
+            P->msgs.push_back(md);
+            blk += m.nblocks;
+        }
+        G.msg_end = (uint32_t)P->msgs.size();
+        G.blocks = blk;
+        const uint64_t gt = (blk + tile_blocks - 1) / tile_blocks;
+        if (tiles + gt > 0xFFFFFFF0u) return fail(AES_ERR_ARG, "batch needs too many tiles");
+        G.tile_start = (uint32_t)tiles;
+        G.tile_end = (uint32_t)(tiles + gt);
+        // first message of each tile: walk the group's messages once
+        uint32_t m = G.msg_start;
+        for (uint64_t lt = 0; lt < gt; ++lt) {
+            const uint64_t first = lt * tile_blocks;
+            while (m + 1 < G.msg_end && P->msgs[m + 1].blk_start <= first) ++m;
+            P->tile_msg.push_back(m);
+        }
+        tiles += gt;
+        P->total_blocks += blk;
+    }
+    P->ntiles = (uint32_t)tiles;
+    if (with_keys) {
+        P->keys.assign(2 * nctx * kSlotWords, 0u);
+        for (size_t i = 0; i < nctx; ++i) {
+            const int words = 4 * (ctxs[i]->nr + 1);
+            memcpy(&P->keys[(2 * i) * kSlotWords], ctxs[i]->enc_rk, 4 * words);
+            memcpy(&P->keys[(2 * i + 1) * kSlotWords], ctxs[i]->dec_rk, 4 * words);
+        }
+    }
+    return AES_OK;
+}
+
+}  // namespace gbaes
+
+using namespace gbaes;
+
+struct aes_batch_plan {
+    uint32_t magic;
+    int device;
+    int threads, bpt;
+    HostPlan host;
+    uint8_t* dev_buf;
+    size_t dev_bytes;
+    BatchArgs args;  // device pointers filled in; in/out set per launch
+    cudaGraphExec_t graph_exec;
+    cudaGraph_t graph;
+    cudaGraphNode_t kernel_node;
+    cudaStream_t capture_stream;
+    std::mutex mu;
+};
+
+namespace gbaes {
+
+constexpr uint32_t kPlanMagic = 0x504c414eu;  // "PLAN"
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+using BatchKernel = void (*)(const BatchArgs);
+
+static BatchKernel pick_batch(int bpt) {
+    switch (bpt) {
+        case 1: return batch_kernel<1>;
+        case 2: return batch_kernel<2>;
+        case 4: return batch_kernel<4>;
+        default: return nullptr;
+    }
+}
+
+int device_status_word(int** p);  // ecb_table.cu
+
+static int check_bases(const HostPlan& H, const void* in_base, size_t in_bytes, const void* out_base,
+                       size_t out_bytes) {
+    if (in_bytes < H.in_extent || out_bytes < H.out_extent)
+        return fail(AES_ERR_ARG, "buffers (%zu in, %zu out bytes) are smaller than the messages need (%llu, %llu)",
+                    in_bytes, out_bytes, (unsigned long long)H.in_extent, (unsigned long long)H.out_extent);
+    if (H.ntiles) {
+        int rc = check_device_range(in_base, H.in_extent, "in_base");
+        if (rc) return rc;
+        rc = check_device_range(out_base, H.out_extent, "out_base");
+        if (rc) return rc;
+    }
+    return AES_OK;
+}
+
+static int plan_launch_args(aes_batch_plan* P, const void* in_base, size_t in_bytes, void* out_base,
+                            size_t out_bytes, BatchArgs* a) {
+    if (!P || P->magic != kPlanMagic) return fail(AES_ERR_ARG, "invalid aes_batch_plan");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device)
+        return fail(AES_ERR_ARG, "plan was built on device %d, current device is %d", P->device, dev);
+    int rc = check_bases(P->host, in_base, in_bytes, out_base, out_bytes);
+    if (rc) return rc;
+    *a = P->args;
+    a->in = (const uint4*)in_base;
+    a->out = (uint4*)out_base;
+    return AES_OK;
+}
+
+static int batch_smem(BatchKernel fn, int* smem) {
+    DeviceInfo info;
+    int rc = current_device_info(&info);
+    if (rc) return rc;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, info.smem_optin);
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    *smem = info.smem_optin;
+    return AES_OK;
+}
+
+static unsigned batch_grid(uint32_t ntiles) {
+    DeviceInfo info;
+    if (current_device_info(&info)) return 1;
+    return (unsigned)std::min<uint64_t>(ntiles, (uint64_t)info.sms);
+}
+
+}  // namespace gbaes
+
+extern "C" {
+
+aes_batch_plan* aes_batch_plan_create(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx,
+                                      int threads, int blocks_per_thread) {
+    if (threads == 0) threads = 1024;
+    if (blocks_per_thread == 0) blocks_per_thread = 2;
+    if (threads < 64 || threads > 1024 || threads % 32) {
+        fail(AES_ERR_ARG, "threads %d: need a multiple of 32 in [64, 1024]", threads);
+        return nullptr;
+    }
+    if (!pick_batch(blocks_per_thread)) {
+        fail(AES_ERR_ARG, "blocks_per_thread %d: need 1, 2 or 4", blocks_per_thread);
+        return nullptr;
+    }
+    aes_batch_plan* P = new (std::nothrow) aes_batch_plan();
+    if (!P) {
+        fail(AES_ERR_NOMEM, "out of host memory");
+        return nullptr;
+    }
+    P->threads = threads;
+    P->bpt = blocks_per_thread;
+    if (build_host_plan(msgs, nmsg, ctxs, nctx, (uint32_t)(threads * blocks_per_thread), true, &P->host)) {
+        delete P;
+        return nullptr;
+    }
+    if (cudaGetDevice(&P->device) != cudaSuccess) {
+        fail(AES_ERR_CUDA, "no CUDA device");
+        delete P;
+        return nullptr;
+    }
+    const HostPlan& H = P->host;
+    const size_t off_keys = 256;
+    const size_t off_msgs = off_keys + align256(H.keys.size() * 4);
+    const size_t off_tiles = off_msgs + align256(H.msgs.size() * sizeof(MsgDev));
+    P->dev_bytes = off_tiles + align256(H.tile_msg.size() * 4 + 4);
+    cudaError_t e = cudaMalloc(&P->dev_buf, P->dev_bytes);
+    if (e != cudaSuccess) {
+        fail(AES_ERR_NOMEM, "cudaMalloc(%zu): %s", P->dev_bytes, cudaGetErrorString(e));
+        delete P;
+        return nullptr;
+    }
+    std::vector<uint8_t> img(P->dev_bytes, 0);
+    if (!H.keys.empty()) memcpy(img.data() + off_keys, H.keys.data(), H.keys.size() * 4);
+    if (!H.msgs.empty()) memcpy(img.data() + off_msgs, H.msgs.data(), H.msgs.size() * sizeof(MsgDev));
+    if (!H.tile_msg.empty()) memcpy(img.data() + off_tiles, H.tile_msg.data(), H.tile_msg.size() * 4);
+    e = cudaMemcpy(P->dev_buf, img.data(), P->dev_bytes, cudaMemcpyHostToDevice);
+    int* status = nullptr;
+    if (e != cudaSuccess || device_status_word(&status)) {
+        fail(AES_ERR_CUDA, "uploading the batch plan: %s", cudaGetErrorString(e));
+        cudaFree(P->dev_buf);
+        delete P;
+        return nullptr;
+    }
+    BatchArgs& a = P->args;
+    memset(&a, 0, sizeof a);
+    a.msgs = (const MsgDev*)(P->dev_buf + off_msgs);
+    a.keys = (const uint4*)(P->dev_buf + off_keys);
+    a.tile_msg = (const uint32_t*)(P->dev_buf + off_tiles);
+    a.counter = (unsigned*)P->dev_buf;
+    a.status = status;
+    a.ntiles = H.ntiles;
+    a.tile_blocks = H.tile_blocks;
+    memcpy(a.groups, H.groups, sizeof a.groups);
+    P->magic = kPlanMagic;
+    return P;
+}
+
+int aes_batch_plan_launch(aes_batch_plan* P, const void* in_base, size_t in_bytes, void* out_base, size_t out_bytes,
+                          void* stream) {
+    BatchArgs a;
+    int rc = plan_launch_args(P, in_base, in_bytes, out_base, out_bytes, &a);
+    if (rc) return rc;
+    if (P->host.ntiles == 0) return AES_OK;
+    BatchKernel fn = pick_batch(P->bpt);
+    int smem = 0;
+    rc = batch_smem(fn, &smem);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "resetting the tile counter: %s", cudaGetErrorString(e));
+    fn<<<batch_grid(P->host.ntiles), P->threads, smem, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "batch kernel launch: %s", cudaGetErrorString(e));
+    return AES_OK;
+}
+
+int aes_batch_plan_launch_graph(aes_batch_plan* P, const void* in_base, size_t in_bytes, void* out_base,
+                                size_t out_bytes, void* stream) {
+    BatchArgs a;
+    int rc = plan_launch_args(P, in_base, in_bytes, out_base, out_bytes, &a);
+    if (rc) return rc;
+    if (P->host.ntiles == 0) return AES_OK;
+    std::lock_guard<std::mutex> lk(P->mu);
+    BatchKernel fn = pick_batch(P->bpt);
+    int smem = 0;
+    rc = batch_smem(fn, &smem);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    if (!P->graph_exec) {
+        if (!P->capture_stream) {
+            e = cudaStreamCreateWithFlags(&P->capture_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return fail(AES_ERR_CUDA, "capture stream: %s", cudaGetErrorString(e));
+        }
+        e = cudaStreamBeginCapture(P->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemsetAsync(a.counter, 0, sizeof(unsigned), P->capture_stream);
+            fn<<<batch_grid(P->host.ntiles), P->threads, smem, P->capture_stream>>>(a);
+            e = cudaStreamEndCapture(P->capture_stream, &P->graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&P->graph_exec, P->graph, 0);
+        if (e == cudaSuccess) {
+            size_t n = 0;
+            cudaGraphGetNodes(P->graph, nullptr, &n);
+            std::vector<cudaGraphNode_t> nodes(n);
+            cudaGraphGetNodes(P->graph, nodes.data(), &n);
+            for (auto node : nodes) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(node, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+                    P->kernel_node = node;
+            }
+        }
+        if (e != cudaSuccess || !P->kernel_node) {
+            cudaGetLastError();
+            return fail(AES_ERR_CUDA, "capturing the batch graph: %s", cudaGetErrorString(e));
+        }
+    } else {
+        void* params[1] = {&a};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof kp);
+        kp.func = (void*)fn;
+        kp.gridDim = dim3(batch_grid(P->host.ntiles));
+        kp.blockDim = dim3(P->threads);
+        kp.sharedMemBytes = smem;
+        kp.kernelParams = params;
+        e = cudaGraphExecKernelNodeSetParams(P->graph_exec, P->kernel_node, &kp);
+        if (e != cudaSuccess) return fail(AES_ERR_CUDA, "updating the batch graph: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphLaunch(P->graph_exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+    return AES_OK;
+}
+
+int aes_batch_plan_info(const aes_batch_plan* P, uint64_t* total_blocks, uint32_t* ntiles, uint32_t* tile_blocks) {
+    if (!P || P->magic != kPlanMagic) return fail(AES_ERR_ARG, "invalid aes_batch_plan");
+    if (total_blocks) *total_blocks = P->host.total_blocks;
+    if (ntiles) *ntiles = P->host.ntiles;
+    if (tile_blocks) *tile_blocks = P->host.tile_blocks;
+    return AES_OK;
+}
+
+void aes_batch_plan_free(aes_batch_plan* P) {
+    if (!P || P->magic != kPlanMagic) return;
+    P->magic = 0;
+    if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
+    cudaFree(P->dev_buf);
+    delete P;
+}
+
+int aes_ecb_batch(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx, const void* in_base,
+                  size_t in_bytes, void* out_base, size_t out_bytes, void* stream) {
+    HostPlan H;
+    int rc = build_host_plan(msgs, nmsg, ctxs, nctx, 2048, true, &H);
+    if (rc) return rc;
+    if (H.ntiles == 0) return AES_OK;
+    rc = check_bases(H, in_base, in_bytes, out_base, out_bytes);
+    if (rc) return rc;
+    // Stream-ordered scratch: plan tables live only as long as the launch.
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t off_keys = 256;
+    const size_t off_msgs = off_keys + align256(H.keys.size() * 4);
+    const size_t off_tiles = off_msgs + align256(H.msgs.size() * sizeof(MsgDev));
+    const size_t bytes = off_tiles + align256(H.tile_msg.size() * 4 + 4);
+    std::vector<uint8_t> img(bytes, 0);
+    memcpy(img.data() + off_keys, H.keys.data(), H.keys.size() * 4);
+    memcpy(img.data() + off_msgs, H.msgs.data(), H.msgs.size() * sizeof(MsgDev));
+    memcpy(img.data() + off_tiles, H.tile_msg.data(), H.tile_msg.size() * 4);
+    uint8_t* buf = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&buf, bytes, s);
+    if (e != cudaSuccess) return fail(AES_ERR_NOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+    e = cudaMemcpyAsync(buf, img.data(), bytes, cudaMemcpyHostToDevice, s);  // pageable: staged before return
+    int* status = nullptr;
+    if (e != cudaSuccess || device_status_word(&status)) {
+        cudaFreeAsync(buf, s);
+        return fail(AES_ERR_CUDA, "uploading the batch tables: %s", cudaGetErrorString(e));
+    }
+    BatchArgs a;
+    memset(&a, 0, sizeof a);
+    a.in = (const uint4*)in_base;
+    a.out = (uint4*)out_base;
+    a.msgs = (const MsgDev*)(buf + off_msgs);
+    a.keys = (const uint4*)(buf + off_keys);
+    a.tile_msg = (const uint32_t*)(buf + off_tiles);
+    a.counter = (unsigned*)buf;
+    a.status = status;
+    a.ntiles = H.ntiles;
+    a.tile_blocks = H.tile_blocks;
+    memcpy(a.groups, H.groups, sizeof a.groups);
+    BatchKernel fn = pick_batch(2);
+    int smem = 0;
+    rc = batch_smem(fn, &smem);
+    if (rc) {
+        cudaFreeAsync(buf, s);
+        return rc;
+    }
+    fn<<<batch_grid(H.ntiles), 1024, smem, s>>>(a);
+    e = cudaGetLastError();
+    cudaFreeAsync(buf, s);
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "batch kernel launch: %s", cudaGetErrorString(e));
+    return AES_OK;
+}
+
+int aes_batch_tiles(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx, int tile_blocks,
+                    uint32_t* first_msg, size_t cap) {
+    if (tile_blocks <= 0) return fail(AES_ERR_ARG, "tile_blocks must be positive");
+    HostPlan H;
+    int rc = build_host_plan(msgs, nmsg, ctxs, nctx, (uint32_t)tile_blocks, false, &H);
+    if (rc) return rc;
+    if (first_msg) {
+        if (cap < H.ntiles) return fail(AES_ERR_ARG, "first_msg holds %zu entries, the batch has %u tiles", cap, H.ntiles);
+        for (uint32_t t = 0; t < H.ntiles; ++t) first_msg[t] = H.msgs[H.tile_msg[t]].src;
+    }
+    return (int)std::min<uint32_t>(H.ntiles, 0x7FFFFFFF);
+}
+
+}  // extern "C"
