@@ -168,6 +168,27 @@ void aes_batch_plan_free(aes_batch_plan* plan);
 int aes_ecb_batch(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx, const void* in_base,
                   size_t in_bytes, void* out_base, size_t out_bytes, void* stream);
 
+/* Batch without device allocation (the paper has no counterpart; this entry
+ * point exists for callers that cannot call cudaMalloc -- code whose device
+ * memory belongs to another runtime or allocator, or latency-critical paths
+ * that must not pay for an allocation).  Same arguments, rules and kernel as
+ * aes_ecb_batch, but the plan tables and the tile counter live in one fixed
+ * 8 MiB device array inside this library instead of freshly allocated memory:
+ *  - Nothing is allocated on the device: no cudaMalloc/cudaFree, no memory
+ *    pool.  The array exists on every GPU that loads the library, until exit.
+ *  - A batch whose tables exceed 8 MiB (512 bytes per key context, 32 bytes per
+ *    message, 4 bytes per 2048-block tile, plus 256) is rejected with
+ *    AES_ERR_ARG; the 10,000-message, 10,000-key batch needs about 5.6 MiB.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and overwrites it (the tile counter is
+ *    re-zeroed by each call's upload).  Calls whose work overlaps on the GPU
+ *    -- on different streams, or from different host threads -- race on it;
+ *    issue them on one stream or otherwise order them. */
+int aes_ecb_batch_noalloc(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx,
+                          const void* in_base, size_t in_bytes, void* out_base, size_t out_bytes, void* stream);
+
 /* Default kernel variant for aes_encrypt_ecb / aes_decrypt_ecb (process-wide;
  * AES_KERNEL_TABLE at start).  Returns the previous variant or AES_ERR_ARG. */
 int aes_set_kernel(int which);

@@ -588,3 +588,102 @@ int aes_batch_tiles(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const*
 }
 
 }  // extern "C"
+
+// ------------------------------------------------ batch without allocation
+//
+// Some callers cannot call cudaMalloc: code whose device memory is owned by
+// another runtime or allocator (a cudaMalloc behind its back breaks its
+// accounting, or fails once it has reserved the device), and latency-critical
+// paths that must not pay an allocation's synchronisation or unbounded cost.
+// aes_ecb_batch_noalloc serves them: it runs the same batched kernel as
+// aes_ecb_batch, but its plan tables and tile counter live in the fixed array
+// below, which every GPU that loads this library holds until the process exits.
+
+namespace gbaes {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;  // 8 MiB
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static uint8_t* g_noalloc_addr[64];  // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch array on the current device.  Host code must
+// not pass the array's own name to a kernel: on the host that name denotes a
+// host-side stand-in, not device memory.  Looked up once per device.
+static int noalloc_scratch(uint8_t** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return fail(AES_ERR_CUDA, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(AES_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = (uint8_t*)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return AES_OK;
+}
+
+}  // namespace gbaes
+
+extern "C" {
+
+int aes_ecb_batch_noalloc(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx,
+                          const void* in_base, size_t in_bytes, void* out_base, size_t out_bytes, void* stream) {
+    HostPlan H;
+    int rc = build_host_plan(msgs, nmsg, ctxs, nctx, 2048, true, &H);
+    if (rc) return rc;
+    if (H.ntiles == 0) return AES_OK;
+    rc = check_bases(H, in_base, in_bytes, out_base, out_bytes);
+    if (rc) return rc;
+    const size_t off_keys = 256;  // [0, 256): tile counter, uploaded as zero
+    const size_t off_msgs = off_keys + align256(H.keys.size() * 4);
+    const size_t off_tiles = off_msgs + align256(H.msgs.size() * sizeof(MsgDev));
+    const size_t bytes = off_tiles + align256(H.tile_msg.size() * 4 + 4);
+    if (bytes > kNoAllocScratchBytes)
+        return fail(AES_ERR_ARG,
+                    "batch needs %zu bytes of tables (keys: 512 B per context; 32 B per message; 4 B per tile), "
+                    "the allocation-free entry point holds at most %zu",
+                    bytes, kNoAllocScratchBytes);
+    uint8_t* buf = nullptr;
+    rc = noalloc_scratch(&buf);
+    if (rc) return rc;
+    int* status = nullptr;
+    rc = device_status_word(&status);
+    if (rc) return rc;
+    BatchKernel fn = pick_batch(2);
+    int smem = 0;
+    rc = batch_smem(fn, &smem);
+    if (rc) return rc;
+    std::vector<uint8_t> img(bytes, 0);  // host staging only; the counter word stays zero
+    memcpy(img.data() + off_keys, H.keys.data(), H.keys.size() * 4);
+    memcpy(img.data() + off_msgs, H.msgs.data(), H.msgs.size() * sizeof(MsgDev));
+    memcpy(img.data() + off_tiles, H.tile_msg.data(), H.tile_msg.size() * 4);
+    cudaStream_t s = (cudaStream_t)stream;
+    // Stream-ordered after earlier work on `stream`; from pageable memory the
+    // call returns once the image is staged, so img may be released after it.
+    cudaError_t e = cudaMemcpyAsync(buf, img.data(), bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "uploading the batch tables: %s", cudaGetErrorString(e));
+    BatchArgs a;
+    memset(&a, 0, sizeof a);
+    a.in = (const uint4*)in_base;
+    a.out = (uint4*)out_base;
+    a.msgs = (const MsgDev*)(buf + off_msgs);
+    a.keys = (const uint4*)(buf + off_keys);
+    a.tile_msg = (const uint32_t*)(buf + off_tiles);
+    a.counter = (unsigned*)buf;
+    a.status = status;
+    a.ntiles = H.ntiles;
+    a.tile_blocks = H.tile_blocks;
+    memcpy(a.groups, H.groups, sizeof a.groups);
+    fn<<<batch_grid(H.ntiles), 1024, smem, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "batch kernel launch: %s", cudaGetErrorString(e));
+    return AES_OK;
+}
+
+}  // extern "C"
