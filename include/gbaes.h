@@ -189,6 +189,30 @@ int aes_ecb_batch(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* c
 int aes_ecb_batch_noalloc(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx,
                           const void* in_base, size_t in_bytes, void* out_base, size_t out_bytes, void* stream);
 
+/* ------------------------------------------------------- host pipeline
+ * ECB on data in host memory (Section 3 copies every texture over the bus and
+ * Fig. 3 shows those copies dominating small inputs).  A pipeline owns `depth`
+ * device staging slots of chunk_bytes each (0, 0 = 64 MiB x 4), each with its
+ * own stream; chunks go round-robin over the slots (copy in, in-place table
+ * kernel, copy out), so copies in both directions overlap the kernels. */
+typedef struct aes_pipeline aes_pipeline;
+
+/* Allocates the staging slots on the current device (cudaMalloc).  chunk_bytes:
+ * multiple of 16; depth: 1..16.  NULL on error. */
+aes_pipeline* aes_pipeline_create(size_t chunk_bytes, int depth);
+
+/* ECB over nblocks blocks from host_in to host_out: page-locked host memory
+ * (cudaHostAlloc / cudaHostRegister; device memory also works), each covering
+ * 16*nblocks bytes (AES_ERR_ARG otherwise); host_in == host_out allowed.
+ * Asynchronous on `stream`: the stream waits for every chunk's copy-out, so
+ * host_out is complete once the stream is.  One pipeline serves one call at a
+ * time (calls from several threads serialise on it). */
+int aes_pipeline_ecb(aes_pipeline* pipe, const aes_ctx* ctx, int decrypt, const void* host_in, void* host_out,
+                     size_t nblocks, void* stream);
+
+/* Waits for the pipeline's streams, then frees it.  NULL is ignored. */
+void aes_pipeline_free(aes_pipeline* pipe);
+
 /* Default kernel variant for aes_encrypt_ecb / aes_decrypt_ecb (process-wide;
  * AES_KERNEL_TABLE at start).  Returns the previous variant or AES_ERR_ARG. */
 int aes_set_kernel(int which);

@@ -36,6 +36,7 @@ __all__ = [
     "BatchPlan",
     "ecb_batch",
     "batch_tiles",
+    "Pipeline",
     "KERNEL_TABLE",
     "KERNEL_BITSLICED",
     "CTR_BE128",
@@ -100,6 +101,10 @@ def _declare(lib):
         "aes_batch_plan_free": (None, [vp]),
         "aes_ecb_batch": (c.c_int, [vp, sz, vp, sz, vp, sz, vp, sz, vp]),
         "aes_batch_tiles": (c.c_int, [vp, sz, vp, sz, c.c_int, u32p, sz]),
+        "aes_ecb_batch_noalloc": (c.c_int, [vp, sz, vp, sz, vp, sz, vp, sz, vp]),
+        "aes_pipeline_create": (vp, [sz, c.c_int]),
+        "aes_pipeline_ecb": (c.c_int, [vp, vp, c.c_int, vp, vp, sz, vp]),
+        "aes_pipeline_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -359,3 +364,35 @@ def batch_tiles(descs: np.ndarray, keys, tile_blocks: int) -> np.ndarray:
     _check(lib.aes_batch_tiles(ctypes.c_void_p(descs.ctypes.data), descs.size, ctxs, len(keys), int(tile_blocks),
                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), out.size))
     return out[:n]
+
+
+# ------------------------------------------------------------- host pipeline
+
+
+class Pipeline:
+    """ECB on page-locked host buffers through device staging slots (aes_pipeline)."""
+
+    def __init__(self, chunk_bytes: int = 64 << 20, depth: int = 4):
+        self._lib = load()
+        h = self._lib.aes_pipeline_create(int(chunk_bytes), int(depth))
+        if not h:
+            _check(-1)
+        self._h = ctypes.c_void_p(h)
+
+    def ecb(self, key: Key, host_in, host_out=None, decrypt: bool = False, stream=None):
+        """host_in/host_out: pinned CPU tensors (torch.empty(..., pin_memory=True))."""
+        import torch
+
+        if host_out is None:
+            host_out = torch.empty_like(host_in).pin_memory()
+        if host_out.numel() * host_out.element_size() != host_in.numel() * host_in.element_size():
+            raise ValueError("host_out must have the same byte size as host_in")
+        _check(self._lib.aes_pipeline_ecb(self._h, key.handle, int(bool(decrypt)), _ptr(host_in), _ptr(host_out),
+                                          _nblocks(host_in), _stream_handle(stream)))
+        return host_out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.aes_pipeline_free(h)
+            self._h = None

@@ -143,6 +143,8 @@ int check_device_range(const void* p, size_t bytes, const char* what) {
     }
     if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged && attr.type != cudaMemoryTypeHost)
         return fail(AES_ERR_ARG, "%s (%p) is not device, managed or page-locked host memory", what, p);
+    if (attr.type == cudaMemoryTypeHost && attr.devicePointer != p)
+        return fail(AES_ERR_ARG, "%s (%p): page-locked memory is not mapped at the same device address", what, p);
     PointerAttrFn get = pointer_attr_fn();
     if (!get) return fail(AES_ERR_CUDA, "cuPointerGetAttribute unavailable: cannot check the extent of %s", what);
     CUdeviceptr start = 0;
@@ -172,6 +174,14 @@ static int bits_index(int bits) { return bits == 128 ? 0 : bits == 192 ? 1 : bit
 static Tuning get_tuning(int bits, int decrypt) {
     std::lock_guard<std::mutex> lk(g_tuning_mu);
     return g_tuning[bits_index(bits)][decrypt ? 1 : 0];
+}
+
+int table_default_shape(int bits, int decrypt, int* threads, int* bpt) {
+    if (bits_index(bits) < 0) return fail(AES_ERR_KEYSIZE, "key size %d bits is not 128, 192 or 256", bits);
+    Tuning t = get_tuning(bits, decrypt);
+    *threads = t.threads;
+    *bpt = t.bpt;
+    return AES_OK;
 }
 
 static bool valid_threads(int t) { return t >= 64 && t <= 1024 && t % 32 == 0; }

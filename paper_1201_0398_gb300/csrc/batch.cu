@@ -71,6 +71,13 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const GroupDev& G
     uint64_t oidx[BPT];
     const uint4* kp[BPT];
     bool ok[BPT];
+    // Tiles inside one message (the common case) read its descriptor once.
+    uint4 q0 = make_uint4(0, 0, 0, 0), q1 = make_uint4(0, 0, 0, 0);
+    if (m_lo == m_hi) {
+        const uint4* mp = (const uint4*)(a.msgs + m_lo);
+        q0 = __ldg(mp);
+        q1 = __ldg(mp + 1);
+    }
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
         const uint64_t gb = gb0 + threadIdx.x + (uint64_t)b * blockDim.x;
@@ -79,7 +86,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const GroupDev& G
         kp[b] = nullptr;
         oidx[b] = 0;
         if (ok[b]) {
-            uint32_t m = m_lo;
+            uint4 r0 = q0, r1 = q1;
             if (m_hi != m_lo) {  // largest m in [m_lo, m_hi] with blk_start[m] <= gb
                 uint32_t lo = m_lo, hi = m_hi;
                 while (lo < hi) {
@@ -89,17 +96,17 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const GroupDev& G
                     else
                         hi = mid - 1;
                 }
-                m = lo;
+                const uint4* mp = (const uint4*)(a.msgs + lo);
+                r0 = __ldg(mp);
+                r1 = __ldg(mp + 1);
             }
-            const uint4* mp = (const uint4*)(a.msgs + m);
-            const uint4 q0 = __ldg(mp), q1 = __ldg(mp + 1);
-            const uint64_t blk_start = ((uint64_t)q0.y << 32) | q0.x;
-            const uint64_t in_blk = ((uint64_t)q0.w << 32) | q0.z;
-            const uint64_t out_blk = ((uint64_t)q1.y << 32) | q1.x;
+            const uint64_t blk_start = ((uint64_t)r0.y << 32) | r0.x;
+            const uint64_t in_blk = ((uint64_t)r0.w << 32) | r0.z;
+            const uint64_t out_blk = ((uint64_t)r1.y << 32) | r1.x;
             const uint64_t off = gb - blk_start;
             v = __ldcs(a.in + in_blk + off);
             oidx[b] = out_blk + off;
-            kp[b] = a.keys + (uint64_t)q1.z * (kSlotWords / 4);
+            kp[b] = a.keys + (uint64_t)r1.z * (kSlotWords / 4);
         }
         s[b][0] = v.x;
         s[b][1] = v.y;
@@ -144,7 +151,7 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const uint32_t base = smem_base(smem_raw);
     const uint32_t A = table_base(base);
-    const uint32_t slot = (base + dynamic_smem_bytes() - 16u) & ~15u;  // tile-index broadcast word
+    const uint32_t slot = (base + dynamic_smem_bytes() - 16u) & ~15u;  // two tile-index broadcast words
     const uint32_t gaddr = slot - 32u * kGroups;                        // group table
     if (A + kDecBytes > gaddr) {
         if (threadIdx.x == 0) atomicOr(a.status, 2);
@@ -160,20 +167,26 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
             for (int k = 0; k < 8; ++k) sts(gaddr + 32u * i + 4u * k, w[k]);
         }
     }
+    if (threadIdx.x == 0) sts(slot, atomicAdd(a.counter, 1u));
+    __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t L0 = A | (lane << 2);
     const uint32_t L1 = L0 | 128u;
     int cur_dir = -1;
-    for (;;) {
-        if (threadIdx.x == 0) sts(slot, atomicAdd(a.counter, 1u));
-        __syncthreads();
-        const uint32_t t = lds(slot);
-        __syncthreads();
+    // Tile i's index sits in slot word (i & 1).  Thread 0 asks for tile i+1
+    // before working on tile i, so the atomic's round trip overlaps the work,
+    // and publishes it in the other word; one barrier per tile then suffices
+    // (word (i & 1) is next written for tile i+2, after that barrier).
+    for (uint32_t i = 0;; ++i) {
+        const uint32_t t = lds(slot + 4u * (i & 1u));
         if (t >= a.ntiles) break;
+        unsigned next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(a.counter, 1u);
         int g = 0;
         while (g < kGroups - 1 && t >= lds(gaddr + 32u * g + 4u)) ++g;  // tile_end of group g
         const GroupDev G = load_group(gaddr, g);
         if (G.dir != cur_dir) {  // CTA-uniform: every thread saw the same t
+            __syncthreads();      // no thread still reads the old tables
             fill_tables(A, G.dir != 0);
             __syncthreads();
             cur_dir = G.dir;
@@ -187,6 +200,8 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
             case 29: batch_tile<14, true, BPT>(a, G, t, L0, L1); break;
             default: break;
         }
+        if (threadIdx.x == 0) sts(slot + 4u * ((i + 1u) & 1u), next);
+        __syncthreads();
     }
 }
 
