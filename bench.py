@@ -21,6 +21,9 @@ six launches, 6 GiB of plaintext-equivalent bytes per step and GPU.  The buffers
   batched   10,000 messages (log-uniform 16 B - 4 MiB, own key each, key sizes
             2:1:1, mixed directions) in one persistent launch, against the same
             messages issued as 10,000 single-message launches.
+  serving   open-loop Poisson arrivals (200k req/s for 10 s, 64 B - 1 MiB, 1,024
+            resident keys, 8 GiB budget) through the continuous-batching server:
+            GB/s and p50/p99 latency from scheduled arrival to completion.
 
 Launch shapes of the table kernel are chosen by the autotuner during setup
 (untimed) and reported under "tuned_shapes".
@@ -64,6 +67,8 @@ def parse_args():
     p.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     p.add_argument("--no-batched", action="store_true", help="skip the batched (10,000-message) section")
     p.add_argument("--batch-steps", type=int, default=10)
+    p.add_argument("--no-serving", action="store_true", help="skip the serving (open-loop) section")
+    p.add_argument("--serve-seconds", type=float, default=10.0)
     return p.parse_args()
 
 
@@ -393,6 +398,14 @@ def run_ours(args):
         torch.cuda.empty_cache()
         batched = bench_batched(g, args, stream, world, rank)
 
+    serving = None
+    if not args.no_serving:
+        torch.cuda.empty_cache()
+        from paper_1201_0398_gb300 import serving as serving_mod
+
+        serving = serving_mod.run(duration_s=args.serve_seconds, seed=workloads.SEED_SERVE + 97 * rank)
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = 64 * MiB
@@ -414,7 +427,7 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(ops) * args.steps,
             "clocks": clk, "ops": op_stats, "tuned_shapes": {k: f"{v['threads']}x{v['blocks_per_thread']}"
                                                              for k, v in tuned.items()},
-            "batched": batched,
+            "batched": batched, "serving": serving,
         }), flush=True)
     if world > 1:
         import torch.distributed as dist

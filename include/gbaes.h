@@ -213,6 +213,98 @@ int aes_pipeline_ecb(aes_pipeline* pipe, const aes_ctx* ctx, int decrypt, const 
 /* Waits for the pipeline's streams, then frees it.  NULL is ignored. */
 void aes_pipeline_free(aes_pipeline* pipe);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous-batching server (pattern: serving).  Section 3.1 finds per-call
+ * overhead dominating small inputs and Section 4 advises against small
+ * messages on the GPU; the server batches requests as they arrive instead:
+ * a scheduler thread admits requests in arrival order while the input+output
+ * bytes of admitted, unfinished requests fit the device-memory budget, packs
+ * them into one batched-kernel launch per free stream slot (batches on
+ * different slots overlap on the device), and completes a batch's requests as
+ * soon as its event fires, freeing budget and slot for requests that arrived
+ * meanwhile.  Key schedules stay resident on the device for the server's
+ * life.  Request data are device pointers owned by the caller, which must keep
+ * them valid until the request completes. */
+
+#define AES_SERVER_DRYRUN 1 /* no GPU work: batches complete at the scheduler's next pass */
+
+typedef struct aes_server aes_server;
+
+typedef struct aes_server_config {
+    uint64_t budget_bytes;      /* in+out bytes in flight (0 = 8 GiB) */
+    int32_t nstreams;           /* stream slots, 1..64 (0 = 4) */
+    int32_t flags;              /* AES_SERVER_* */
+    int32_t threads;            /* batched-kernel CTA size (0 = 512) */
+    int32_t blocks_per_thread;  /* 1, 2 or 4 (0 = 1) */
+    uint32_t max_batch_msgs;    /* requests per batch (0 = 4096) */
+    uint32_t reserved;
+    uint64_t max_batch_blocks;  /* blocks per batch, also the largest request (0 = 2^22) */
+} aes_server_config;
+
+typedef struct aes_server_request {
+    uint64_t id;        /* caller's tag, returned in the completion */
+    const void* in;     /* device pointer, 16-byte aligned, 16*nblocks bytes */
+    void* out;          /* device pointer; in == out allowed */
+    uint64_t nblocks;
+    uint32_t key_index; /* index into the server's keys */
+    uint32_t decrypt;   /* 0 = encrypt, 1 = decrypt */
+    double arrival_s;   /* replay only: scheduled arrival, seconds after the replay starts */
+} aes_server_request;
+
+typedef struct aes_server_completion {
+    uint64_t id;
+    int32_t status;      /* AES_OK, or the error the request failed with */
+    uint32_t batch_msgs; /* requests in its batch */
+    double arrival_s;    /* arrival (scheduled, for replays) on the server clock, seconds */
+    double launch_s;     /* launch of its batch */
+    double done_s;       /* when its completion was observed */
+} aes_server_completion;
+
+typedef struct aes_server_stats {
+    uint64_t submitted, completed, failed, rejected, batches;
+    uint64_t max_inflight_bytes; /* peak admitted in+out bytes (never above the budget) */
+    uint64_t max_queue;          /* peak requests waiting for admission */
+    uint64_t max_batch_msgs;
+    uint64_t budget_bytes;
+} aes_server_stats;
+
+/* Creates a server on the current device with nkeys resident key contexts
+ * (copied; the caller may free them afterwards) and starts its scheduler
+ * thread.  config may be NULL for the defaults.  NULL on error. */
+aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const aes_server_config* config);
+
+/* Queues one request (arrival = now).  Checks its pointers and sizes on the
+ * host; a request whose in+out bytes exceed the budget, or whose blocks
+ * exceed max_batch_blocks, is refused with AES_ERR_BUDGET. */
+int aes_server_submit(aes_server* server, const aes_server_request* req);
+
+/* Starts a producer thread that submits reqs[i] at arrival_s[i] seconds after
+ * the call (open loop: late submissions keep their scheduled arrival time, so
+ * queueing delay is counted).  The array is copied.  One replay at a time. */
+int aes_server_replay(aes_server* server, const aes_server_request* reqs, size_t n);
+
+/* Waits for the replay thread (stop_early != 0: ends it after its current request). */
+int aes_server_replay_join(aes_server* server, int stop_early);
+
+/* Waits until every submitted request has completed (timeout_s < 0: forever).
+ * AES_ERR_STATE on timeout. */
+int aes_server_drain(aes_server* server, double timeout_s);
+
+/* Moves up to max completions into out; returns how many. */
+int aes_server_poll(aes_server* server, aes_server_completion* out, size_t max);
+
+/* Copies the server's counters. */
+int aes_server_get_stats(aes_server* server, aes_server_stats* out);
+
+/* Test hook: the batch with this index (0-based, in launch order) fails as if
+ * its launch had returned an error; its requests complete with
+ * AES_ERR_DEVICE and the server carries on. */
+int aes_server_inject_fault(aes_server* server, uint64_t batch_index);
+
+/* Stops the replay, finishes every queued request, stops the scheduler and
+ * frees the server.  NULL is ignored. */
+void aes_server_destroy(aes_server* server);
+
 /* Default kernel variant for aes_encrypt_ecb / aes_decrypt_ecb (process-wide;
  * AES_KERNEL_TABLE at start).  Returns the previous variant or AES_ERR_ARG. */
 int aes_set_kernel(int which);

@@ -37,6 +37,10 @@ __all__ = [
     "ecb_batch",
     "batch_tiles",
     "Pipeline",
+    "Server",
+    "SERVER_DRYRUN",
+    "REQUEST",
+    "COMPLETION",
     "KERNEL_TABLE",
     "KERNEL_BITSLICED",
     "CTR_BE128",
@@ -105,6 +109,15 @@ def _declare(lib):
         "aes_pipeline_create": (vp, [sz, c.c_int]),
         "aes_pipeline_ecb": (c.c_int, [vp, vp, c.c_int, vp, vp, sz, vp]),
         "aes_pipeline_free": (None, [vp]),
+        "aes_server_create": (vp, [vp, sz, vp]),
+        "aes_server_submit": (c.c_int, [vp, vp]),
+        "aes_server_replay": (c.c_int, [vp, vp, sz]),
+        "aes_server_replay_join": (c.c_int, [vp, c.c_int]),
+        "aes_server_drain": (c.c_int, [vp, c.c_double]),
+        "aes_server_poll": (c.c_int, [vp, vp, sz]),
+        "aes_server_get_stats": (c.c_int, [vp, vp]),
+        "aes_server_inject_fault": (c.c_int, [vp, c.c_uint64]),
+        "aes_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -396,3 +409,88 @@ class Pipeline:
         if h is not None and h.value:
             self._lib.aes_pipeline_free(h)
             self._h = None
+
+
+# ------------------------------------------------------------------- serving
+
+SERVER_DRYRUN = 1
+
+# Match aes_server_request / aes_server_completion (48 and 40 bytes).
+REQUEST = np.dtype([("id", "<u8"), ("in_ptr", "<u8"), ("out_ptr", "<u8"), ("nblocks", "<u8"), ("key_index", "<u4"),
+                    ("decrypt", "<u4"), ("arrival_s", "<f8")])
+COMPLETION = np.dtype([("id", "<u8"), ("status", "<i4"), ("batch_msgs", "<u4"), ("arrival_s", "<f8"),
+                       ("launch_s", "<f8"), ("done_s", "<f8")])
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("nstreams", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("blocks_per_thread", ctypes.c_int32), ("max_batch_msgs", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("max_batch_blocks", ctypes.c_uint64)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "rejected", "batches",
+                                               "max_inflight_bytes", "max_queue", "max_batch_msgs", "budget_bytes")]
+
+
+class Server:
+    """Continuous-batching server (aes_server) with resident keys."""
+
+    def __init__(self, keys, budget_bytes: int = 8 << 30, nstreams: int = 4, threads: int = 0,
+                 blocks_per_thread: int = 0, max_batch_msgs: int = 0, max_batch_blocks: int = 0, dryrun: bool = False):
+        self._lib = load()
+        self._keys = list(keys)
+        cfg = _ServerConfig(int(budget_bytes), int(nstreams), SERVER_DRYRUN if dryrun else 0, int(threads),
+                            int(blocks_per_thread), int(max_batch_msgs), 0, int(max_batch_blocks))
+        h = self._lib.aes_server_create(_ctx_array(self._keys), len(self._keys), ctypes.byref(cfg))
+        if not h:
+            _check(-1)
+        self._h = ctypes.c_void_p(h)
+
+    def submit(self, req_id: int, key_index: int, in_ptr: int, out_ptr: int, nblocks: int, decrypt: bool = False):
+        r = np.zeros(1, REQUEST)
+        r["id"], r["in_ptr"], r["out_ptr"], r["nblocks"] = req_id, in_ptr, out_ptr, nblocks
+        r["key_index"], r["decrypt"] = key_index, int(bool(decrypt))
+        _check(self._lib.aes_server_submit(self._h, ctypes.c_void_p(r.ctypes.data)))
+
+    def replay(self, reqs: np.ndarray):
+        """Open-loop replay of a REQUEST array (arrival_s non-decreasing) on a native thread."""
+        self._replay = np.ascontiguousarray(reqs, REQUEST)
+        _check(self._lib.aes_server_replay(self._h, ctypes.c_void_p(self._replay.ctypes.data), self._replay.size))
+
+    def replay_join(self, stop_early: bool = False):
+        _check(self._lib.aes_server_replay_join(self._h, int(bool(stop_early))))
+
+    def drain(self, timeout_s: float = -1.0):
+        _check(self._lib.aes_server_drain(self._h, float(timeout_s)))
+
+    def poll(self, max_items: int = 1 << 22) -> np.ndarray:
+        out = np.zeros(max_items, COMPLETION)
+        n = _check(self._lib.aes_server_poll(self._h, ctypes.c_void_p(out.ctypes.data), max_items))
+        return out[:n]
+
+    def poll_all(self) -> np.ndarray:
+        parts = []
+        while True:
+            p = self.poll()
+            if p.size == 0:
+                break
+            parts.append(p)
+        return np.concatenate(parts) if parts else np.zeros(0, COMPLETION)
+
+    def stats(self) -> dict:
+        s = _ServerStats()
+        _check(self._lib.aes_server_get_stats(self._h, ctypes.byref(s)))
+        return {n: getattr(s, n) for n, _ in s._fields_}
+
+    def inject_fault(self, batch_index: int):
+        _check(self._lib.aes_server_inject_fault(self._h, int(batch_index)))
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.aes_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

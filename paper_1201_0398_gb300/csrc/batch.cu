@@ -26,40 +26,9 @@
 #include <vector>
 
 #include "aes_rounds.cuh"
+#include "batch_plan.h"
 
 namespace gbaes {
-
-struct MsgDev {  // 32 bytes, group order
-    uint64_t blk_start;  // first block of the message in its group's block space
-    uint64_t in_blk;     // in_off / 16
-    uint64_t out_blk;    // out_off / 16
-    uint32_t key_slot;   // schedule slot (2 * key_index + decrypt)
-    uint32_t src;        // caller's message index
-};
-
-struct GroupDev {
-    uint32_t tile_start, tile_end;  // tiles [tile_start, tile_end)
-    uint32_t msg_start, msg_end;    // messages [msg_start, msg_end) in group order
-    uint64_t blocks;                // blocks in the group
-    int32_t nr;
-    int32_t dir;  // 0 encrypt, 1 decrypt
-};
-
-constexpr int kGroups = 6;
-constexpr int kSlotWords = 64;  // 60 used (Nr = 14), padded to 256 bytes
-
-struct BatchArgs {
-    const uint4* in;
-    uint4* out;
-    const MsgDev* msgs;
-    const uint4* keys;  // kSlotWords / 4 uint4 per slot
-    const uint32_t* tile_msg;
-    unsigned* counter;
-    int* status;
-    uint32_t ntiles;
-    uint32_t tile_blocks;
-    GroupDev groups[kGroups];
-};
 
 template <int NR, bool DEC, int BPT>
 __device__ __forceinline__ void batch_tile(const BatchArgs& a, const GroupDev& G, uint32_t t, uint32_t L0,
@@ -207,22 +176,10 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
 
 // ------------------------------------------------------------------ host plan
 
-struct HostPlan {
-    std::vector<MsgDev> msgs;
-    std::vector<uint32_t> tile_msg;
-    std::vector<uint32_t> keys;  // 2 * nctx slots of kSlotWords words
-    GroupDev groups[kGroups];
-    uint32_t ntiles = 0;
-    uint32_t tile_blocks = 0;
-    uint64_t total_blocks = 0;
-    uint64_t in_extent = 0;   // bytes from in_base the plan reads
-    uint64_t out_extent = 0;  // bytes from out_base the plan writes
-};
-
 static int group_of(int nr, int dir) { return dir * 3 + (nr == 10 ? 0 : nr == 12 ? 1 : 2); }
 
 // Validates the descriptors and lays out groups, tiles and key slots.
-static int build_host_plan(const aes_msg_desc* d, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx,
+int build_host_plan(const aes_msg_desc* d, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx,
                            uint32_t tile_blocks, bool with_keys, HostPlan* P) {
     if (nmsg && !d) return fail(AES_ERR_ARG, "message descriptors are NULL");
     if (nctx && !ctxs) return fail(AES_ERR_ARG, "key contexts are NULL");
@@ -328,7 +285,6 @@ static BatchKernel pick_batch(int bpt) {
     }
 }
 
-int device_status_word(int** p);  // ecb_table.cu
 
 static int check_bases(const HostPlan& H, const void* in_base, size_t in_bytes, const void* out_base,
                        size_t out_bytes) {
@@ -372,6 +328,18 @@ static unsigned batch_grid(uint32_t ntiles) {
     DeviceInfo info;
     if (current_device_info(&info)) return 1;
     return (unsigned)std::min<uint64_t>(ntiles, (uint64_t)info.sms);
+}
+
+int launch_batch_kernel(const BatchArgs& a, int threads, int bpt, cudaStream_t stream) {
+    BatchKernel fn = pick_batch(bpt);
+    if (!fn) return fail(AES_ERR_ARG, "blocks_per_thread %d: need 1, 2 or 4", bpt);
+    int smem = 0;
+    int rc = batch_smem(fn, &smem);
+    if (rc) return rc;
+    fn<<<batch_grid(a.ntiles), threads, smem, stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "batch kernel launch: %s", cudaGetErrorString(e));
+    return AES_OK;
 }
 
 }  // namespace gbaes

@@ -1,0 +1,482 @@
+// Continuous-batching AES server (pattern: serving).
+//
+// The paper advises against using the GPU for small messages because each
+// operation pays a large fixed overhead (Section 3.1; Section 4).  The server
+// answers that with continuous batching:
+//
+//  * Requests (key index, direction, device in/out pointers, length) arrive at
+//    any time through aes_server_submit, or from a replay thread that issues a
+//    recorded open-loop arrival schedule at its scheduled times.
+//  * One scheduler thread admits requests in arrival order while the bytes in
+//    flight (input + output of every admitted, unfinished request) stay within
+//    the device-memory budget, packs them into a micro-batch, and launches it
+//    through the batched kernel (batch.cu) on a free stream slot.  Batches on
+//    different slots run concurrently on the device; as soon as a slot's event
+//    fires, its requests complete, their bytes leave the budget, and the slot
+//    takes the next batch -- requests that arrived meanwhile are admitted then.
+//  * Expanded key schedules are resident on the device for the server's life;
+//    a batch carries only its message and tile tables (a few hundred bytes per
+//    request), copied from pinned staging on the slot's stream.
+//  * Latency is completion time minus arrival time (the scheduled arrival for
+//    replays, so a slow server cannot hide queueing delay).
+//
+// A dry-run mode replaces every CUDA call with an immediate completion so the
+// scheduling logic (admission, budget, batching, fault handling, drain) can be
+// exercised on a machine without a GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "batch_plan.h"
+
+namespace gbaes {
+
+constexpr uint32_t kServerMagic = 0x53525652u;  // "SRVR"
+
+struct Pending {
+    aes_server_request r;
+    double arrival;  // seconds on the server clock
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    uint8_t* dev_buf = nullptr;
+    uint8_t* host_buf = nullptr;
+    std::vector<Pending> reqs;
+    double launch_s = 0;
+    uint64_t bytes = 0;
+    bool busy = false;
+};
+
+}  // namespace gbaes
+
+using namespace gbaes;
+
+struct aes_server {
+    uint32_t magic = 0;
+    aes_server_config cfg{};
+    int device = 0;
+    bool dryrun = false;
+    std::vector<aes_ctx> keys;          // host copies (key sizes, schedules)
+    std::vector<const aes_ctx*> key_ptrs;
+    uint4* dev_keys = nullptr;          // resident schedules: slot 2k = enc, 2k+1 = dec
+    int* status = nullptr;
+    size_t slot_cap = 0;
+    std::vector<Slot> slots;
+    std::chrono::steady_clock::time_point t0;
+
+    std::mutex in_mu;
+    std::vector<Pending> inbox;
+    std::deque<Pending> queue;  // scheduler thread only
+    uint64_t inflight_bytes = 0;  // scheduler thread only
+    uint64_t batch_counter = 0;   // scheduler thread only
+
+    std::mutex out_mu;
+    std::vector<aes_server_completion> done;
+
+    std::mutex stats_mu;
+    aes_server_stats stats{};
+
+    std::atomic<uint64_t> submitted{0};
+    std::atomic<uint64_t> finished{0};
+    std::atomic<uint64_t> fault_batch{UINT64_MAX};
+    std::atomic<bool> stop{false};
+    std::atomic<bool> producer_stop{false};
+    std::atomic<bool> producer_running{false};
+    std::thread scheduler;
+    std::thread producer;
+    std::vector<aes_server_request> replay_reqs;
+    double replay_start = 0;
+
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace gbaes {
+
+static void complete(aes_server* S, std::vector<Pending>& reqs, int status, double launch_s, double done_s) {
+    std::vector<aes_server_completion> out;
+    out.reserve(reqs.size());
+    for (const Pending& p : reqs) {
+        aes_server_completion c;
+        c.id = p.r.id;
+        c.status = status;
+        c.batch_msgs = (uint32_t)reqs.size();
+        c.arrival_s = p.arrival;
+        c.launch_s = launch_s;
+        c.done_s = done_s;
+        out.push_back(c);
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->out_mu);
+        S->done.insert(S->done.end(), out.begin(), out.end());
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->stats_mu);
+        S->stats.completed += reqs.size();
+        if (status != AES_OK) S->stats.failed += reqs.size();
+    }
+    S->finished.fetch_add(reqs.size());
+    reqs.clear();
+}
+
+static uint64_t request_bytes(const aes_server_request& r) { return 32ull * r.nblocks; }
+
+// Launches one micro-batch on a free slot.  Returns AES_OK or the error with
+// which the batch's requests are completed.
+static int launch_slot(aes_server* S, Slot& slot) {
+    const uint64_t index = S->batch_counter++;
+    if (index == S->fault_batch.load()) return fail(AES_ERR_DEVICE, "injected fault on batch %llu", (unsigned long long)index);
+    if (S->dryrun) return AES_OK;
+    std::vector<aes_msg_desc> d(slot.reqs.size());
+    for (size_t i = 0; i < slot.reqs.size(); ++i) {
+        const aes_server_request& r = slot.reqs[i].r;
+        d[i].in_off = (uint64_t)(uintptr_t)r.in;  // absolute addresses: the kernel's base pointers are 0
+        d[i].out_off = (uint64_t)(uintptr_t)r.out;
+        d[i].nblocks = r.nblocks;
+        d[i].key_index = r.key_index;
+        d[i].decrypt = r.decrypt;
+    }
+    HostPlan H;
+    const uint32_t tb = (uint32_t)(S->cfg.threads * S->cfg.blocks_per_thread);
+    int rc = build_host_plan(d.data(), d.size(), S->key_ptrs.data(), S->key_ptrs.size(), tb, false, &H);
+    if (rc) return rc;
+    if (H.ntiles == 0) return AES_OK;
+    const size_t off_msgs = 256;
+    const size_t off_tiles = off_msgs + ((H.msgs.size() * sizeof(MsgDev) + 255) & ~(size_t)255);
+    const size_t bytes = off_tiles + H.tile_msg.size() * 4 + 4;
+    if (bytes > S->slot_cap) return fail(AES_ERR_ARG, "batch tables (%zu B) exceed the slot (%zu B)", bytes, S->slot_cap);
+    memset(slot.host_buf, 0, 256);
+    memcpy(slot.host_buf + off_msgs, H.msgs.data(), H.msgs.size() * sizeof(MsgDev));
+    memcpy(slot.host_buf + off_tiles, H.tile_msg.data(), H.tile_msg.size() * 4);
+    cudaError_t e = cudaMemcpyAsync(slot.dev_buf, slot.host_buf, bytes, cudaMemcpyHostToDevice, slot.stream);
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "batch table upload: %s", cudaGetErrorString(e));
+    BatchArgs a;
+    memset(&a, 0, sizeof a);
+    a.in = nullptr;
+    a.out = nullptr;
+    a.msgs = (const MsgDev*)(slot.dev_buf + off_msgs);
+    a.keys = S->dev_keys;
+    a.tile_msg = (const uint32_t*)(slot.dev_buf + off_tiles);
+    a.counter = (unsigned*)slot.dev_buf;
+    a.status = S->status;
+    a.ntiles = H.ntiles;
+    a.tile_blocks = H.tile_blocks;
+    memcpy(a.groups, H.groups, sizeof a.groups);
+    rc = launch_batch_kernel(a, S->cfg.threads, S->cfg.blocks_per_thread, slot.stream);
+    if (rc) return rc;
+    e = cudaEventRecord(slot.done, slot.stream);
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "batch event: %s", cudaGetErrorString(e));
+    return AES_OK;
+}
+
+static void scheduler_main(aes_server* S) {
+    if (!S->dryrun) cudaSetDevice(S->device);
+    for (;;) {
+        bool worked = false;
+        {
+            std::lock_guard<std::mutex> lk(S->in_mu);
+            if (!S->inbox.empty()) {
+                for (Pending& p : S->inbox) S->queue.push_back(p);
+                S->inbox.clear();
+                worked = true;
+            }
+        }
+        // Completions.
+        for (Slot& slot : S->slots) {
+            if (!slot.busy) continue;
+            int st = AES_OK;
+            if (!S->dryrun) {
+                cudaError_t q = cudaEventQuery(slot.done);
+                if (q == cudaErrorNotReady) continue;
+                if (q != cudaSuccess) st = AES_ERR_CUDA;
+            }
+            const double t = S->now();
+            S->inflight_bytes -= slot.bytes;
+            slot.bytes = 0;
+            slot.busy = false;
+            complete(S, slot.reqs, st, slot.launch_s, t);
+            worked = true;
+        }
+        // Admission in arrival order, then launch on free slots.
+        for (Slot& slot : S->slots) {
+            if (slot.busy || S->queue.empty()) continue;
+            uint64_t blocks = 0, bytes = 0;
+            while (!S->queue.empty() && slot.reqs.size() < S->cfg.max_batch_msgs) {
+                const Pending& p = S->queue.front();
+                const uint64_t b = request_bytes(p.r);
+                if (S->inflight_bytes + bytes + b > S->cfg.budget_bytes) break;
+                if (!slot.reqs.empty() && blocks + p.r.nblocks > S->cfg.max_batch_blocks) break;
+                blocks += p.r.nblocks;
+                bytes += b;
+                slot.reqs.push_back(p);
+                S->queue.pop_front();
+            }
+            if (slot.reqs.empty()) break;  // the budget is full: wait for completions
+            slot.launch_s = S->now();
+            int rc = launch_slot(S, slot);
+            if (rc != AES_OK && !S->dryrun) cudaStreamSynchronize(slot.stream);  // staging may still be read
+            {
+                std::lock_guard<std::mutex> lk(S->stats_mu);
+                S->stats.batches++;
+                S->stats.max_batch_msgs = std::max<uint64_t>(S->stats.max_batch_msgs, slot.reqs.size());
+            }
+            if (rc != AES_OK) {
+                complete(S, slot.reqs, rc, slot.launch_s, S->now());
+            } else {
+                slot.busy = true;
+                slot.bytes = bytes;
+                S->inflight_bytes += bytes;
+                std::lock_guard<std::mutex> lk(S->stats_mu);
+                S->stats.max_inflight_bytes = std::max<uint64_t>(S->stats.max_inflight_bytes, S->inflight_bytes);
+            }
+            worked = true;
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->stats_mu);
+            S->stats.max_queue = std::max<uint64_t>(S->stats.max_queue, S->queue.size());
+        }
+        if (!worked) {
+            bool idle = S->queue.empty();
+            for (const Slot& slot : S->slots) idle = idle && !slot.busy;
+            if (idle && S->stop.load()) {
+                std::lock_guard<std::mutex> lk(S->in_mu);
+                if (S->inbox.empty()) break;
+            }
+            std::this_thread::yield();
+        }
+    }
+}
+
+static int enqueue(aes_server* S, const aes_server_request& r, double arrival) {
+    if (r.key_index >= S->keys.size())
+        return fail(AES_ERR_ARG, "request %llu: key_index %u >= %zu", (unsigned long long)r.id, r.key_index,
+                    S->keys.size());
+    if (r.decrypt > 1) return fail(AES_ERR_ARG, "request %llu: decrypt must be 0 or 1", (unsigned long long)r.id);
+    if (r.nblocks > (UINT64_MAX >> 6)) return fail(AES_ERR_ARG, "request %llu: nblocks too large", (unsigned long long)r.id);
+    if (request_bytes(r) > S->cfg.budget_bytes || r.nblocks > S->cfg.max_batch_blocks) {
+        std::lock_guard<std::mutex> lk(S->stats_mu);
+        S->stats.rejected++;
+        return fail(AES_ERR_BUDGET, "request %llu: %llu blocks exceed the server's budget or batch limit",
+                    (unsigned long long)r.id, (unsigned long long)r.nblocks);
+    }
+    if (!S->dryrun && r.nblocks) {
+        const size_t bytes = (size_t)r.nblocks * 16;
+        int rc = check_device_range(r.in, bytes, "request in");
+        if (!rc) rc = check_device_range(r.out, bytes, "request out");
+        if (rc) return rc;
+        const uintptr_t i0 = (uintptr_t)r.in, o0 = (uintptr_t)r.out;
+        if (i0 != o0 && i0 < o0 + bytes && o0 < i0 + bytes) return fail(AES_ERR_ARG, "request in/out overlap partially");
+    } else if (((uintptr_t)r.in | (uintptr_t)r.out) & 15u) {
+        return fail(AES_ERR_ALIGN, "request %llu: pointers must be 16-byte aligned", (unsigned long long)r.id);
+    }
+    S->submitted.fetch_add(1);
+    {
+        std::lock_guard<std::mutex> lk(S->stats_mu);
+        S->stats.submitted++;
+    }
+    std::lock_guard<std::mutex> lk(S->in_mu);
+    S->inbox.push_back(Pending{r, arrival});
+    return AES_OK;
+}
+
+static void producer_main(aes_server* S) {
+    const double start = S->now();
+    S->replay_start = start;
+    for (const aes_server_request& r : S->replay_reqs) {
+        if (S->producer_stop.load()) break;
+        const double due = start + r.arrival_s;
+        for (;;) {  // wait for the scheduled arrival time
+            const double wait = due - S->now();
+            if (wait <= 0) break;
+            if (wait > 200e-6)
+                std::this_thread::sleep_for(std::chrono::duration<double>(wait - 100e-6));
+            else
+                std::this_thread::yield();
+            if (S->producer_stop.load()) break;
+        }
+        if (S->producer_stop.load()) break;
+        const int rc = enqueue(S, r, due);
+        if (rc != AES_OK) {  // rejected requests complete at once with their error
+            aes_server_completion c{r.id, rc, 0, due, due, S->now()};
+            std::lock_guard<std::mutex> lk(S->out_mu);
+            S->done.push_back(c);
+        }
+    }
+    S->producer_running.store(false);
+}
+
+static void destroy_server(aes_server* S) {
+    for (Slot& slot : S->slots) {
+        if (slot.done) cudaEventDestroy(slot.done);
+        if (slot.stream) cudaStreamDestroy(slot.stream);
+        if (slot.dev_buf) cudaFree(slot.dev_buf);
+        if (slot.host_buf) cudaFreeHost(slot.host_buf);
+    }
+    if (S->dev_keys) cudaFree(S->dev_keys);
+    delete S;
+}
+
+}  // namespace gbaes
+
+extern "C" {
+
+aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const aes_server_config* config) {
+    aes_server_config cfg;
+    memset(&cfg, 0, sizeof cfg);
+    if (config) cfg = *config;
+    if (cfg.budget_bytes == 0) cfg.budget_bytes = (uint64_t)8 << 30;
+    if (cfg.nstreams == 0) cfg.nstreams = 4;
+    if (cfg.threads == 0) cfg.threads = 512;
+    if (cfg.blocks_per_thread == 0) cfg.blocks_per_thread = 1;
+    if (cfg.max_batch_msgs == 0) cfg.max_batch_msgs = 4096;
+    if (cfg.max_batch_blocks == 0) cfg.max_batch_blocks = (uint64_t)1 << 22;
+    if (cfg.nstreams < 1 || cfg.nstreams > 64 || cfg.threads < 64 || cfg.threads > 1024 || cfg.threads % 32 ||
+        (cfg.blocks_per_thread != 1 && cfg.blocks_per_thread != 2 && cfg.blocks_per_thread != 4) ||
+        cfg.max_batch_msgs > (1u << 20)) {
+        fail(AES_ERR_ARG, "invalid server configuration");
+        return nullptr;
+    }
+    if (nkeys == 0 || !keys) {
+        fail(AES_ERR_ARG, "a server needs at least one key");
+        return nullptr;
+    }
+    for (size_t i = 0; i < nkeys; ++i)
+        if (!keys[i] || keys[i]->magic != kCtxMagic) {
+            fail(AES_ERR_ARG, "keys[%zu] is not a valid aes_ctx", i);
+            return nullptr;
+        }
+    aes_server* S = new (std::nothrow) aes_server();
+    if (!S) {
+        fail(AES_ERR_NOMEM, "out of host memory");
+        return nullptr;
+    }
+    S->cfg = cfg;
+    S->dryrun = (cfg.flags & AES_SERVER_DRYRUN) != 0;
+    S->keys.assign(nkeys, aes_ctx{});
+    for (size_t i = 0; i < nkeys; ++i) S->keys[i] = *keys[i];
+    for (size_t i = 0; i < nkeys; ++i) S->key_ptrs.push_back(&S->keys[i]);
+    S->slots.resize(cfg.nstreams);
+    const uint64_t tb = (uint64_t)cfg.threads * cfg.blocks_per_thread;
+    S->slot_cap = 256 + (((size_t)cfg.max_batch_msgs * sizeof(MsgDev) + 255) & ~(size_t)255) +
+                  4 * (size_t)(cfg.max_batch_blocks / tb + 8) + 4;
+    if (!S->dryrun) {
+        cudaError_t e = cudaGetDevice(&S->device);
+        std::vector<uint32_t> img(2 * nkeys * 64, 0u);
+        for (size_t i = 0; i < nkeys; ++i) {
+            memcpy(&img[(2 * i) * 64], keys[i]->enc_rk, 4 * 4 * (keys[i]->nr + 1));
+            memcpy(&img[(2 * i + 1) * 64], keys[i]->dec_rk, 4 * 4 * (keys[i]->nr + 1));
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&S->dev_keys, img.size() * 4);
+        if (e == cudaSuccess) e = cudaMemcpy(S->dev_keys, img.data(), img.size() * 4, cudaMemcpyHostToDevice);
+        for (Slot& slot : S->slots) {
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaMalloc(&slot.dev_buf, S->slot_cap);
+            if (e == cudaSuccess) e = cudaMallocHost(&slot.host_buf, S->slot_cap);
+        }
+        if (e != cudaSuccess || device_status_word(&S->status)) {
+            fail(AES_ERR_CUDA, "server setup: %s", cudaGetErrorString(e));
+            cudaGetLastError();
+            destroy_server(S);
+            return nullptr;
+        }
+    }
+    S->stats.budget_bytes = cfg.budget_bytes;
+    S->t0 = std::chrono::steady_clock::now();
+    S->magic = kServerMagic;
+    S->scheduler = std::thread(scheduler_main, S);
+    return S;
+}
+
+static int check_server(aes_server* S) {
+    if (!S || S->magic != kServerMagic) return fail(AES_ERR_ARG, "invalid aes_server");
+    if (S->stop.load()) return fail(AES_ERR_STATE, "server is shutting down");
+    return AES_OK;
+}
+
+int aes_server_submit(aes_server* S, const aes_server_request* r) {
+    int rc = check_server(S);
+    if (rc) return rc;
+    if (!r) return fail(AES_ERR_ARG, "request is NULL");
+    return enqueue(S, *r, S->now());
+}
+
+int aes_server_replay(aes_server* S, const aes_server_request* reqs, size_t n) {
+    int rc = check_server(S);
+    if (rc) return rc;
+    if (n && !reqs) return fail(AES_ERR_ARG, "requests are NULL");
+    if (S->producer_running.load() || S->producer.joinable())
+        return fail(AES_ERR_STATE, "a replay is already running (join it first)");
+    for (size_t i = 1; i < n; ++i)
+        if (reqs[i].arrival_s < reqs[i - 1].arrival_s) return fail(AES_ERR_ARG, "arrival times must not decrease");
+    S->replay_reqs.assign(reqs, reqs + n);
+    S->producer_stop.store(false);
+    S->producer_running.store(true);
+    S->producer = std::thread(producer_main, S);
+    return AES_OK;
+}
+
+int aes_server_replay_join(aes_server* S, int stop_early) {
+    if (!S || S->magic != kServerMagic) return fail(AES_ERR_ARG, "invalid aes_server");
+    if (stop_early) S->producer_stop.store(true);
+    if (S->producer.joinable()) S->producer.join();
+    return AES_OK;
+}
+
+int aes_server_drain(aes_server* S, double timeout_s) {
+    if (!S || S->magic != kServerMagic) return fail(AES_ERR_ARG, "invalid aes_server");
+    const double until = S->now() + timeout_s;
+    while (S->finished.load() < S->submitted.load() || S->producer_running.load()) {
+        if (timeout_s >= 0 && S->now() > until) return fail(AES_ERR_STATE, "drain timed out");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    return AES_OK;
+}
+
+int aes_server_poll(aes_server* S, aes_server_completion* out, size_t max) {
+    if (!S || S->magic != kServerMagic) return fail(AES_ERR_ARG, "invalid aes_server");
+    if (max && !out) return fail(AES_ERR_ARG, "out is NULL");
+    std::lock_guard<std::mutex> lk(S->out_mu);
+    const size_t n = std::min(max, S->done.size());
+    if (n > 0x7FFFFFFF) return fail(AES_ERR_ARG, "poll at most 2^31-1 completions at a time");
+    std::copy(S->done.begin(), S->done.begin() + n, out);
+    S->done.erase(S->done.begin(), S->done.begin() + n);
+    return (int)n;
+}
+
+int aes_server_get_stats(aes_server* S, aes_server_stats* out) {
+    if (!S || S->magic != kServerMagic) return fail(AES_ERR_ARG, "invalid aes_server");
+    if (!out) return fail(AES_ERR_ARG, "out is NULL");
+    std::lock_guard<std::mutex> lk(S->stats_mu);
+    *out = S->stats;
+    return AES_OK;
+}
+
+int aes_server_inject_fault(aes_server* S, uint64_t batch_index) {
+    if (!S || S->magic != kServerMagic) return fail(AES_ERR_ARG, "invalid aes_server");
+    S->fault_batch.store(batch_index);
+    return AES_OK;
+}
+
+void aes_server_destroy(aes_server* S) {
+    if (!S || S->magic != kServerMagic) return;
+    S->producer_stop.store(true);
+    if (S->producer.joinable()) S->producer.join();
+    S->stop.store(true);
+    if (S->scheduler.joinable()) S->scheduler.join();
+    S->magic = 0;
+    destroy_server(S);
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+"""Open-loop serving run: Poisson arrivals replayed into the native server.
+
+Requests read slices of one device-resident input pool and write to an output
+ring.  Consecutive requests take consecutive ring space; the ring is larger
+than the output bytes the budget lets be in flight (half the budget) plus the
+largest request, so two requests that are in flight together never share
+output bytes.  Latency is completion minus *scheduled* arrival.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import REQUEST, Key, Server, ecb_ex, workloads
+
+GiB = 1 << 30
+
+
+def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8 << 30, nkeys: int = 1024,
+        nstreams: int = 4, threads: int = 512, blocks_per_thread: int = 1, max_batch_msgs: int = 4096,
+        pool_bytes: int = GiB, check_last: int = 1000, seed: int = workloads.SEED_SERVE) -> dict:
+    import torch
+
+    w = workloads.serve_workload(rate=rate, duration_s=duration_s, nkeys=nkeys, seed=seed)
+    n = w.arrival_s.size
+    keys = [Key(k) for k in w.keys]
+    dev = torch.device("cuda")
+    x = workloads.device_bytes(seed, pool_bytes, device=dev)
+    max_len = int(w.lengths.max())
+    ring = max(2 * (budget_bytes // 2), 4 * GiB) + 2 * max_len
+    ring = (ring + 15) // 16 * 16
+    y = torch.empty(ring + max_len, dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(seed + 1)
+    in_off = rng.integers(0, (pool_bytes - w.lengths) // 16 + 1) * 16
+    cum = np.concatenate([[0], np.cumsum(w.lengths)[:-1]])
+    out_off = cum % ring
+    reqs = np.zeros(n, REQUEST)
+    reqs["id"] = np.arange(n)
+    reqs["in_ptr"] = x.data_ptr() + in_off
+    reqs["out_ptr"] = y.data_ptr() + out_off
+    reqs["nblocks"] = w.lengths // 16
+    reqs["key_index"] = w.key_index
+    reqs["decrypt"] = w.decrypt
+    reqs["arrival_s"] = w.arrival_s
+
+    srv = Server(keys, budget_bytes=budget_bytes, nstreams=nstreams, threads=threads,
+                 blocks_per_thread=blocks_per_thread, max_batch_msgs=max_batch_msgs)
+    srv.replay(reqs)
+    srv.replay_join()
+    srv.drain(120.0)
+    done = srv.poll_all()
+    stats = srv.stats()
+    srv.close()
+    ok = done["status"] == 0
+    lat = (done["done_s"] - done["arrival_s"])[ok]
+    span = float(done["done_s"].max() - done["arrival_s"].min())
+    total = int(w.lengths.sum())
+
+    # The last requests' outputs are still in the ring: compare with the
+    # single-message kernel on each request alone.
+    torch.cuda.synchronize()
+    mismatches = 0
+    idx = np.arange(max(0, n - check_last), n)
+    alone = torch.empty(int(w.lengths[idx].max()), dtype=torch.uint8, device=dev)
+    for i in idx:
+        a, b, m = int(in_off[i]), int(out_off[i]), int(w.lengths[i])
+        ecb_ex(keys[int(w.key_index[i])], x[a:a + m], alone[:m], decrypt=bool(w.decrypt[i]))
+        if not torch.equal(alone[:m], y[b:b + m]):
+            mismatches += 1
+    batches = np.unique(done["launch_s"])
+    return {
+        "value": total / span / 1e9, "unit": "GB/s", "requests": int(n), "completed_ok": int(ok.sum()),
+        "offered_gbs": total / duration_s / 1e9, "bytes": total,
+        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+        "p999_ms": float(np.percentile(lat, 99.9) * 1e3), "max_ms": float(lat.max() * 1e3),
+        "mean_batch_msgs": float(n / max(1, len(batches))), "batches": int(stats["batches"]),
+        "max_queue": int(stats["max_queue"]), "max_inflight_bytes": int(stats["max_inflight_bytes"]),
+        "budget_bytes": int(budget_bytes), "nstreams": nstreams, "shape": f"{threads}x{blocks_per_thread}",
+        "checked_alone": int(len(idx)), "mismatches": mismatches,
+        "workload": f"Poisson {rate:.0f} req/s for {duration_s:g} s, sizes log-uniform 64 B-1 MiB (x16 B), "
+                    f"{nkeys} resident keys (128/192/256), encrypt/decrypt 50/50, {budget_bytes >> 30} GiB budget",
+    }
