@@ -69,6 +69,9 @@ def parse_args():
     p.add_argument("--batch-steps", type=int, default=10)
     p.add_argument("--no-serving", action="store_true", help="skip the serving (open-loop) section")
     p.add_argument("--serve-seconds", type=float, default=10.0)
+    p.add_argument("--sweep", action="store_true",
+                   help="size sweep 4 KiB - 16 GiB (powers of 4), AES-128/256 encrypt, table vs bitsliced kernel")
+    p.add_argument("--sweep-max-gib", type=int, default=16)
     return p.parse_args()
 
 
@@ -491,8 +494,51 @@ def bench_batched(g, args, stream, world, rank):
                         "encrypt/decrypt 50/50, one persistent launch"}
 
 
+def run_sweep(args):
+    """One JSON line per (key size, kernel, buffer size): device-resident
+    uniform random bytes, CUDA-event time per launch (median of reps)."""
+    import torch
+
+    import paper_1201_0398_gb300 as g
+    from paper_1201_0398_gb300 import workloads
+
+    g.load()
+    peaks, peak_kind = measured_peaks()
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    stream = torch.cuda.current_stream()
+    sizes = [4096 * 4 ** i for i in range(12) if 4096 * 4 ** i <= args.sweep_max_gib * GiB]
+    x = workloads.device_bytes(31, sizes[-1])
+    y = torch.empty_like(x)
+    for bits in (128, 256):
+        k = g.Key(workloads.random_key(40 + bits, bits))
+        for kname, kid in (("table", g.KERNEL_TABLE), ("bitsliced", g.KERNEL_BITSLICED)):
+            for size in sizes:
+                xs, ys = x[:size], y[:size]
+                reps = max(5, min(200, int(2 * GiB // size)))
+                for _ in range(3):
+                    g.ecb_ex(k, xs, ys, kernel=kid, stream=stream)
+                times = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    g.ecb_ex(k, xs, ys, kernel=kid, stream=stream)
+                    e1.record(stream)
+                    times.append((e0, e1))
+                torch.cuda.synchronize()
+                ms = statistics.median(a.elapsed_time(b) for a, b in times)
+                gbs = size / (ms / 1e3) / 1e9
+                r_smem = sms * LOOKUPS_PER_CLK_PER_SM * f_max / NR[bits] / 1e9
+                print(json.dumps({"sweep": "aes-ecb-encrypt", "bits": bits, "kernel": kname, "bytes": size,
+                                  "ms": ms, "gbs": gbs, "reps": reps, "frac_smem_roofline": gbs / r_smem,
+                                  "hbm_frac": 2 * gbs / float(peaks["hbm_gbs"])}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

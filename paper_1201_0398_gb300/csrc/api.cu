@@ -240,7 +240,7 @@ static int run_block_op(const aes_ctx* ctx, Mode mode, const void* in, void* out
     if (mode == kCbcDec) memcpy(a.iv, iv, 16);
     if (kernel == AES_KERNEL_BITSLICED) {
         if (mode != kEnc && mode != kDec) return fail(AES_ERR_ARG, "the bitsliced kernel implements ECB only");
-        return launch_bitsliced(a, ctx->nr, mode, threads, (cudaStream_t)stream);
+        return launch_bitsliced(a, ctx->enc_rk, ctx->nr, mode, threads, (cudaStream_t)stream);
     }
     return launch_table(a, ctx->nr, mode, threads, bpt, (cudaStream_t)stream);
 }

@@ -58,7 +58,7 @@ int check_device_range(const void* p, size_t bytes, const char* what);
 int launch_table(const EcbArgs& a, int nr, Mode mode, int threads, int bpt, cudaStream_t stream);
 
 // Launches the bitsliced kernel (ecb_bitsliced.cu), ECB only.
-int launch_bitsliced(const EcbArgs& a, int nr, Mode mode, int threads, cudaStream_t stream);
+int launch_bitsliced(const EcbArgs& a, const uint32_t* enc_rk, int nr, Mode mode, int threads, cudaStream_t stream);
 
 // Library status word on the device (set by kernels that detect an error).
 int read_device_status(int clear);

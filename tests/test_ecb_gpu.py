@@ -218,3 +218,28 @@ def test_sweep_top_sizes_sampled(gbaes, gib):
         del c
     del x
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("bits", BITS)
+def test_bitsliced_kernel_vs_oracle(gbaes, bits):
+    """The Boolean-circuit kernel (32 blocks per thread as bit planes): edge sizes
+    around a warp tile (1,024 blocks) and a multi-CTA run with a ragged tail."""
+    rng = np.random.default_rng(900 + bits)
+    key = rng.integers(0, 256, bits // 8, dtype=np.uint8).tobytes()
+    k = gbaes.Key(key)
+    for n in (1, 31, 32, 33, 1023, 1024, 1025, 4097, sms() * 512 + 3):
+        data = rng.integers(0, 256, 16 * n, dtype=np.uint8)
+        for decrypt in (False, True):
+            for threads in (32, 128):
+                out = gbaes.ecb_ex(k, dev(data), decrypt=decrypt, kernel=gbaes.KERNEL_BITSLICED, threads=threads)
+                assert np.array_equal(host(out), oracle.ecb(key, bits, data, decrypt=decrypt)), (n, decrypt)
+
+
+def test_bitsliced_equals_table_kernel_large(gbaes):
+    x = workloads.device_bytes(77, 256 << 20)
+    for bits in BITS:
+        k = gbaes.Key(workloads.random_key(70 + bits, bits))
+        for decrypt in (False, True):
+            a = gbaes.ecb_ex(k, x, decrypt=decrypt, kernel=gbaes.KERNEL_TABLE)
+            b = gbaes.ecb_ex(k, x, decrypt=decrypt, kernel=gbaes.KERNEL_BITSLICED)
+            assert torch.equal(a, b)
