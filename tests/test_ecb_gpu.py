@@ -230,7 +230,7 @@ def test_bitsliced_kernel_vs_oracle(gbaes, bits):
     for n in (1, 31, 32, 33, 1023, 1024, 1025, 4097, sms() * 512 + 3):
         data = rng.integers(0, 256, 16 * n, dtype=np.uint8)
         for decrypt in (False, True):
-            for threads in (32, 128):
+            for threads in (64, 128):
                 out = gbaes.ecb_ex(k, dev(data), decrypt=decrypt, kernel=gbaes.KERNEL_BITSLICED, threads=threads)
                 assert np.array_equal(host(out), oracle.ecb(key, bits, data, decrypt=decrypt)), (n, decrypt)
 
