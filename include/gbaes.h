@@ -134,16 +134,16 @@ typedef struct aes_batch_plan aes_batch_plan;
 
 /* Builds a reusable plan: validates every descriptor (AES_ERR_ARG /
  * AES_ERR_ALIGN), groups messages by direction and key size, tiles the
- * flattened blocks (threads * blocks_per_thread blocks per tile; 0, 0 =
- * 1024, 2) and uploads the tile table, message table and every context's two
+ * flattened blocks (one tile = 256 * blocks_per_thread blocks, taken by one
+ * warp; CTAs of `threads` threads; 0, 0 = 1024, 2) and uploads the tile table, message table and every context's two
  * schedules to one device allocation on the current device (cudaMalloc,
  * synchronous).  msgs and ctxs are HOST arrays, read during the call only.
  * Returns NULL on error. */
 aes_batch_plan* aes_batch_plan_create(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx,
                                       int threads, int blocks_per_thread);
 
-/* Launches a plan on `stream`: resets the plan's tile counter, then one
- * persistent kernel (one CTA per SM).  in_base/out_base: device buffers of
+/* Launches a plan on `stream`: resets the plan's tile counters, then one
+ * persistent kernel (one CTA per SM; its warps take tiles independently).  in_base/out_base: device buffers of
  * in_bytes/out_bytes bytes that must cover every message (AES_ERR_ARG).  Two
  * launches of the same plan must not run concurrently (they share its tile
  * counter); stream-ordered repeats are fine. */
@@ -234,7 +234,7 @@ typedef struct aes_server_config {
     uint64_t budget_bytes;      /* in+out bytes in flight (0 = 8 GiB) */
     int32_t nstreams;           /* stream slots, 1..64 (0 = 4) */
     int32_t flags;              /* AES_SERVER_* */
-    int32_t threads;            /* batched-kernel CTA size (0 = 512) */
+    int32_t threads;            /* batched-kernel CTA size (0 = 256) */
     int32_t blocks_per_thread;  /* 1, 2 or 4 (0 = 1) */
     uint32_t max_batch_msgs;    /* requests per batch (0 = 4096) */
     uint32_t reserved;

@@ -30,16 +30,15 @@
 
 namespace gbaes {
 
+// One warp's tile: tile_blocks consecutive blocks of group G's block space,
+// processed 32*BPT at a time (lane l, slot b -> block base + 32b + l, so every
+// load and store instruction of the warp covers 512 contiguous bytes).
 template <int NR, bool DEC, int BPT>
-__device__ __forceinline__ void batch_tile(const BatchArgs& a, const GroupDev& G, uint32_t t, uint32_t L0,
-                                           uint32_t L1) {
-    const uint64_t gb0 = (uint64_t)(t - G.tile_start) * a.tile_blocks;
+__device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupDev& G, uint32_t t, uint32_t lane,
+                                                uint32_t L0, uint32_t L1) {
+    const uint64_t tb0 = (uint64_t)(t - G.tile_start) * a.tile_blocks;
     const uint32_t m_lo = a.tile_msg[t];
     const uint32_t m_hi = (t + 1 < G.tile_end) ? a.tile_msg[t + 1] : G.msg_end - 1;
-    uint32_t s[BPT][4];
-    uint64_t oidx[BPT];
-    const uint4* kp[BPT];
-    bool ok[BPT];
     // Tiles inside one message (the common case) read its descriptor once.
     uint4 q0 = make_uint4(0, 0, 0, 0), q1 = make_uint4(0, 0, 0, 0);
     if (m_lo == m_hi) {
@@ -47,59 +46,66 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const GroupDev& G
         q0 = __ldg(mp);
         q1 = __ldg(mp + 1);
     }
-#pragma unroll
-    for (int b = 0; b < BPT; ++b) {
-        const uint64_t gb = gb0 + threadIdx.x + (uint64_t)b * blockDim.x;
-        ok[b] = gb < G.blocks;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        kp[b] = nullptr;
-        oidx[b] = 0;
-        if (ok[b]) {
-            uint4 r0 = q0, r1 = q1;
-            if (m_hi != m_lo) {  // largest m in [m_lo, m_hi] with blk_start[m] <= gb
-                uint32_t lo = m_lo, hi = m_hi;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi + 1) >> 1;
-                    if (__ldg((const unsigned long long*)(a.msgs + mid)) <= gb)
-                        lo = mid;
-                    else
-                        hi = mid - 1;
-                }
-                const uint4* mp = (const uint4*)(a.msgs + lo);
-                r0 = __ldg(mp);
-                r1 = __ldg(mp + 1);
-            }
-            const uint64_t blk_start = ((uint64_t)r0.y << 32) | r0.x;
-            const uint64_t in_blk = ((uint64_t)r0.w << 32) | r0.z;
-            const uint64_t out_blk = ((uint64_t)r1.y << 32) | r1.x;
-            const uint64_t off = gb - blk_start;
-            v = __ldcs(a.in + in_blk + off);
-            oidx[b] = out_blk + off;
-            kp[b] = a.keys + (uint64_t)r1.z * (kSlotWords / 4);
-        }
-        s[b][0] = v.x;
-        s[b][1] = v.y;
-        s[b][2] = v.z;
-        s[b][3] = v.w;
-    }
-    if (!ok[0]) return;  // blocks of a thread are in increasing order: none valid
-    bool same = true;
-#pragma unroll
-    for (int b = 1; b < BPT; ++b) same = same && (!ok[b] || kp[b] == kp[0]);
-    if (same) {
-        cipher<NR, DEC, BPT>(s, GlobalKeys{kp[0]}, L0, L1);
-    } else {
+    for (uint32_t it = 0; it < a.tile_blocks; it += 32u * BPT) {
+        uint32_t s[BPT][4];
+        uint64_t oidx[BPT];
+        const uint4* kp[BPT];
+        bool ok[BPT];
 #pragma unroll
         for (int b = 0; b < BPT; ++b) {
-            if (ok[b]) cipher<NR, DEC, 1>(*reinterpret_cast<uint32_t(*)[1][4]>(&s[b]), GlobalKeys{kp[b]}, L0, L1);
+            const uint64_t gb = tb0 + it + 32u * b + lane;
+            ok[b] = gb < G.blocks && it + 32u * b + lane < a.tile_blocks;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            kp[b] = nullptr;
+            oidx[b] = 0;
+            if (ok[b]) {
+                uint4 r0 = q0, r1 = q1;
+                if (m_hi != m_lo) {  // largest m in [m_lo, m_hi] with blk_start[m] <= gb
+                    uint32_t lo = m_lo, hi = m_hi;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) >> 1;
+                        if (__ldg((const unsigned long long*)(a.msgs + mid)) <= gb)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
+                    }
+                    const uint4* mp = (const uint4*)(a.msgs + lo);
+                    r0 = __ldg(mp);
+                    r1 = __ldg(mp + 1);
+                }
+                const uint64_t blk_start = ((uint64_t)r0.y << 32) | r0.x;
+                const uint64_t in_blk = ((uint64_t)r0.w << 32) | r0.z;
+                const uint64_t out_blk = ((uint64_t)r1.y << 32) | r1.x;
+                const uint64_t off = gb - blk_start;
+                v = __ldcs(a.in + in_blk + off);
+                oidx[b] = out_blk + off;
+                kp[b] = a.keys + (uint64_t)r1.z * (kSlotWords / 4);
+            }
+            s[b][0] = v.x;
+            s[b][1] = v.y;
+            s[b][2] = v.z;
+            s[b][3] = v.w;
         }
-    }
+        if (!ok[0]) return;  // blocks only increase: nothing left in this tile
+        bool same = true;
 #pragma unroll
-    for (int b = 0; b < BPT; ++b)
-        if (ok[b]) __stcs(a.out + oidx[b], make_uint4(s[b][0], s[b][1], s[b][2], s[b][3]));
+        for (int b = 1; b < BPT; ++b) same = same && (!ok[b] || kp[b] == kp[0]);
+        if (same) {
+            cipher<NR, DEC, BPT>(s, GlobalKeys{kp[0]}, L0, L1);
+        } else {
+#pragma unroll
+            for (int b = 0; b < BPT; ++b) {
+                if (ok[b])
+                    cipher<NR, DEC, 1>(*reinterpret_cast<uint32_t(*)[1][4]>(&s[b]), GlobalKeys{kp[b]}, L0, L1);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < BPT; ++b)
+            if (ok[b]) __stcs(a.out + oidx[b], make_uint4(s[b][0], s[b][1], s[b][2], s[b][3]));
+    }
 }
 
-// Group table staged in shared memory (read with a runtime index each tile).
+// Group table staged in shared memory (read with a runtime index per tile).
 __device__ __forceinline__ GroupDev load_group(uint32_t gaddr, int g) {
     GroupDev G;
     uint32_t w[8];
@@ -115,13 +121,18 @@ __device__ __forceinline__ GroupDev load_group(uint32_t gaddr, int g) {
     return G;
 }
 
+// Tiles [0, E) are encryption tiles (groups 0-2), [E, ntiles) decryption
+// tiles, with E = tile_end of group 2.  Every warp takes tiles from the
+// direction's own counter until it runs dry, independently of the other
+// warps, so their global-memory latencies overlap.  The CTA meets at a barrier
+// only to swap its shared-memory tables from the encryption to the decryption
+// set, once.
 template <int BPT>
 __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const uint32_t base = smem_base(smem_raw);
     const uint32_t A = table_base(base);
-    const uint32_t slot = (base + dynamic_smem_bytes() - 16u) & ~15u;  // two tile-index broadcast words
-    const uint32_t gaddr = slot - 32u * kGroups;                        // group table
+    const uint32_t gaddr = ((base + dynamic_smem_bytes()) & ~15u) - 32u * kGroups;  // group table
     if (A + kDecBytes > gaddr) {
         if (threadIdx.x == 0) atomicOr(a.status, 2);
         return;
@@ -136,41 +147,41 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
             for (int k = 0; k < 8; ++k) sts(gaddr + 32u * i + 4u * k, w[k]);
         }
     }
-    if (threadIdx.x == 0) sts(slot, atomicAdd(a.counter, 1u));
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t L0 = A | (lane << 2);
     const uint32_t L1 = L0 | 128u;
+    const uint32_t enc_end = lds(gaddr + 32u * 2 + 4u);  // tile_end of group 2
     int cur_dir = -1;
-    // Tile i's index sits in slot word (i & 1).  Thread 0 asks for tile i+1
-    // before working on tile i, so the atomic's round trip overlaps the work,
-    // and publishes it in the other word; one barrier per tile then suffices
-    // (word (i & 1) is next written for tile i+2, after that barrier).
-    for (uint32_t i = 0;; ++i) {
-        const uint32_t t = lds(slot + 4u * (i & 1u));
-        if (t >= a.ntiles) break;
-        unsigned next = 0;
-        if (threadIdx.x == 0) next = atomicAdd(a.counter, 1u);
-        int g = 0;
-        while (g < kGroups - 1 && t >= lds(gaddr + 32u * g + 4u)) ++g;  // tile_end of group g
-        const GroupDev G = load_group(gaddr, g);
-        if (G.dir != cur_dir) {  // CTA-uniform: every thread saw the same t
-            __syncthreads();      // no thread still reads the old tables
-            fill_tables(A, G.dir != 0);
+    for (int dir = 0; dir < 2; ++dir) {
+        const uint32_t t_begin = dir ? enc_end : 0u;
+        const uint32_t t_end = dir ? a.ntiles : enc_end;
+        if (t_begin >= t_end) continue;  // same for the whole CTA
+        if (dir != cur_dir) {
+            __syncthreads();  // every warp has left the other direction's tiles
+            fill_tables(A, dir != 0);
             __syncthreads();
-            cur_dir = G.dir;
+            cur_dir = dir;
         }
-        switch (G.nr * 2 + G.dir) {
-            case 20: batch_tile<10, false, BPT>(a, G, t, L0, L1); break;
-            case 21: batch_tile<10, true, BPT>(a, G, t, L0, L1); break;
-            case 24: batch_tile<12, false, BPT>(a, G, t, L0, L1); break;
-            case 25: batch_tile<12, true, BPT>(a, G, t, L0, L1); break;
-            case 28: batch_tile<14, false, BPT>(a, G, t, L0, L1); break;
-            case 29: batch_tile<14, true, BPT>(a, G, t, L0, L1); break;
-            default: break;
+        for (;;) {
+            uint32_t t = 0;
+            if (lane == 0) t = atomicAdd(a.counter + dir, 1u);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= t_end - t_begin) break;
+            t += t_begin;
+            int g = 0;
+            while (g < kGroups - 1 && t >= lds(gaddr + 32u * g + 4u)) ++g;  // tile_end of group g
+            const GroupDev G = load_group(gaddr, g);
+            switch (G.nr * 2 + dir) {
+                case 20: batch_warp_tile<10, false, BPT>(a, G, t, lane, L0, L1); break;
+                case 21: batch_warp_tile<10, true, BPT>(a, G, t, lane, L0, L1); break;
+                case 24: batch_warp_tile<12, false, BPT>(a, G, t, lane, L0, L1); break;
+                case 25: batch_warp_tile<12, true, BPT>(a, G, t, lane, L0, L1); break;
+                case 28: batch_warp_tile<14, false, BPT>(a, G, t, lane, L0, L1); break;
+                case 29: batch_warp_tile<14, true, BPT>(a, G, t, lane, L0, L1); break;
+                default: break;
+            }
         }
-        if (threadIdx.x == 0) sts(slot + 4u * ((i + 1u) & 1u), next);
-        __syncthreads();
     }
 }
 
@@ -365,7 +376,7 @@ aes_batch_plan* aes_batch_plan_create(const aes_msg_desc* msgs, size_t nmsg, con
     }
     P->threads = threads;
     P->bpt = blocks_per_thread;
-    if (build_host_plan(msgs, nmsg, ctxs, nctx, (uint32_t)(threads * blocks_per_thread), true, &P->host)) {
+    if (build_host_plan(msgs, nmsg, ctxs, nctx, 256u * (uint32_t)blocks_per_thread, true, &P->host)) {
         delete P;
         return nullptr;
     }
@@ -422,7 +433,7 @@ int aes_batch_plan_launch(aes_batch_plan* P, const void* in_base, size_t in_byte
     rc = batch_smem(fn, &smem);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return fail(AES_ERR_CUDA, "resetting the tile counter: %s", cudaGetErrorString(e));
     fn<<<batch_grid(P->host.ntiles), P->threads, smem, s>>>(a);
     e = cudaGetLastError();
@@ -449,7 +460,7 @@ int aes_batch_plan_launch_graph(aes_batch_plan* P, const void* in_base, size_t i
         }
         e = cudaStreamBeginCapture(P->capture_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaMemsetAsync(a.counter, 0, sizeof(unsigned), P->capture_stream);
+            cudaMemsetAsync(a.counter, 0, 2 * sizeof(unsigned), P->capture_stream);
             fn<<<batch_grid(P->host.ntiles), P->threads, smem, P->capture_stream>>>(a);
             e = cudaStreamEndCapture(P->capture_stream, &P->graph);
         }
