@@ -335,7 +335,7 @@ def run_ours(args):
     dec_dom = dom_name.endswith("dec")
     bpt_dom = tuned.get(dom_name, {}).get("blocks_per_thread", 2)
     ktpl = f"table_kernel<{NR[bits_dom]},{1 if dec_dom else 0},{bpt_dom}>"
-    traffic = dram_traffic(ktpl) if kernel == g.KERNEL_TABLE else None
+    traffic = dram_traffic(f"table_kernel<{NR[bits_dom]},{1 if dec_dom else 0}>") if kernel == g.KERNEL_TABLE else None
     clock_frac = None
     if clk.get("sm_mhz"):
         r_clk = sms * LOOKUPS_PER_CLK_PER_SM * clk["sm_mhz"] * 1e6 / NR[bits_dom] / 1e9
@@ -486,9 +486,14 @@ def bench_batched(g, args, stream, world, rank):
 
     t_loop = timed(single_loop, 2)
     total = w.total_bytes
+    nr_eff = float((w.lengths * np.vectorize(NR.get)(w.bits)).sum() / total)  # lookups per plaintext byte
+    peaks, _ = measured_peaks()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    r_smem = sms * LOOKUPS_PER_CLK_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / nr_eff / 1e9
     return {"value": world * total / t_plan / 1e9, "unit": "GB/s", "messages": len(keys), "bytes": total,
             "ms": 1e3 * t_plan, "graph_gbs": world * total / t_graph / 1e9,
             "single_launch_loop_gbs": world * total / t_loop / 1e9, "shape": report["best"],
+            "nr_eff": nr_eff, "smem_roofline_gbs": r_smem, "frac": total / t_plan / 1e9 / r_smem,
             "candidates_ms": report["candidates_ms"], "launches_per_step": 1,
             "workload": "10,000 messages, log-uniform 16 B-4 MiB (x16 B), keys 128/192/256 at 2:1:1, "
                         "encrypt/decrypt 50/50, one persistent launch"}

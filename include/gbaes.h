@@ -234,7 +234,7 @@ typedef struct aes_server_config {
     uint64_t budget_bytes;      /* in+out bytes in flight (0 = 8 GiB) */
     int32_t nstreams;           /* stream slots, 1..64 (0 = 4) */
     int32_t flags;              /* AES_SERVER_* */
-    int32_t threads;            /* batched-kernel CTA size (0 = 256) */
+    int32_t threads;            /* batched-kernel CTA size (0 = 512) */
     int32_t blocks_per_thread;  /* 1, 2 or 4 (0 = 1) */
     uint32_t max_batch_msgs;    /* requests per batch (0 = 4096) */
     uint32_t reserved;

@@ -148,7 +148,7 @@ static int launch_slot(aes_server* S, Slot& slot) {
         d[i].decrypt = r.decrypt;
     }
     HostPlan H;
-    const uint32_t tb = 128u * (uint32_t)S->cfg.blocks_per_thread;  // warp tiles of 4 passes
+    const uint32_t tb = 32u * (uint32_t)S->cfg.blocks_per_thread;  // one pass per warp tile: low latency
     int rc = build_host_plan(d.data(), d.size(), S->key_ptrs.data(), S->key_ptrs.size(), tb, false, &H);
     if (rc) return rc;
     if (H.ntiles == 0) return AES_OK;
@@ -337,7 +337,7 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
     if (config) cfg = *config;
     if (cfg.budget_bytes == 0) cfg.budget_bytes = (uint64_t)8 << 30;
     if (cfg.nstreams == 0) cfg.nstreams = 4;
-    if (cfg.threads == 0) cfg.threads = 256;
+    if (cfg.threads == 0) cfg.threads = 512;
     if (cfg.blocks_per_thread == 0) cfg.blocks_per_thread = 1;
     if (cfg.max_batch_msgs == 0) cfg.max_batch_msgs = 4096;
     if (cfg.max_batch_blocks == 0) cfg.max_batch_blocks = (uint64_t)1 << 22;
@@ -367,7 +367,7 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
     for (size_t i = 0; i < nkeys; ++i) S->keys[i] = *keys[i];
     for (size_t i = 0; i < nkeys; ++i) S->key_ptrs.push_back(&S->keys[i]);
     S->slots.resize(cfg.nstreams);
-    const uint64_t tb = 128ull * cfg.blocks_per_thread;
+    const uint64_t tb = 32ull * cfg.blocks_per_thread;
     S->slot_cap = 256 + (((size_t)cfg.max_batch_msgs * sizeof(MsgDev) + 255) & ~(size_t)255) +
                   4 * (size_t)(cfg.max_batch_blocks / tb + 8) + 4;
     if (!S->dryrun) {

@@ -16,7 +16,7 @@ GiB = 1 << 30
 
 
 def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8 << 30, nkeys: int = 1024,
-        nstreams: int = 4, threads: int = 512, blocks_per_thread: int = 1, max_batch_msgs: int = 4096,
+        nstreams: int = 4, threads: int = 0, blocks_per_thread: int = 1, max_batch_msgs: int = 4096,
         pool_bytes: int = GiB, check_last: int = 1000, seed: int = workloads.SEED_SERVE) -> dict:
     import torch
 
@@ -74,7 +74,7 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
         "p999_ms": float(np.percentile(lat, 99.9) * 1e3), "max_ms": float(lat.max() * 1e3),
         "mean_batch_msgs": float(n / max(1, len(batches))), "batches": int(stats["batches"]),
         "max_queue": int(stats["max_queue"]), "max_inflight_bytes": int(stats["max_inflight_bytes"]),
-        "budget_bytes": int(budget_bytes), "nstreams": nstreams, "shape": f"{threads}x{blocks_per_thread}",
+        "budget_bytes": int(budget_bytes), "nstreams": nstreams, "shape": f"{threads or 512}x{blocks_per_thread}",
         "checked_alone": int(len(idx)), "mismatches": mismatches,
         "workload": f"Poisson {rate:.0f} req/s for {duration_s:g} s, sizes log-uniform 64 B-1 MiB (x16 B), "
                     f"{nkeys} resident keys (128/192/256), encrypt/decrypt 50/50, {budget_bytes >> 30} GiB budget",
