@@ -30,10 +30,46 @@
 
 namespace gbaes {
 
+// Same cipher with the round count known only at run time: one compact loop
+// body serves every key size (used where several key sizes share a kernel and
+// the round keys come from memory anyway).
+template <bool DECRYPT, int BPT, class KS>
+__device__ __forceinline__ void cipher_rt(uint32_t (&s)[BPT][4], const KS& ks, int nr, uint32_t L0, uint32_t L1) {
+    {
+        const uint4 k = ks.get(0);
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            s[b][0] ^= k.x;
+            s[b][1] ^= k.y;
+            s[b][2] ^= k.z;
+            s[b][3] ^= k.w;
+        }
+    }
+#pragma unroll 1
+    for (int r = 1; r < nr; ++r) {
+        const uint4 k = ks.get(r);
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            if (DECRYPT)
+                dec_round(s[b], L0, L1, k);
+            else
+                enc_round(s[b], L0, L1, k);
+        }
+    }
+    const uint4 k = ks.get(nr);
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        if (DECRYPT)
+            dec_last(s[b], L0, k);
+        else
+            enc_last(s[b], L0, L1, k);
+    }
+}
+
 // One warp's tile: tile_blocks consecutive blocks of group G's block space,
 // processed 32*BPT at a time (lane l, slot b -> block base + 32b + l, so every
 // load and store instruction of the warp covers 512 contiguous bytes).
-template <int NR, bool DEC, int BPT>
+template <bool DEC, int BPT>
 __device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupDev& G, uint32_t t, uint32_t lane,
                                                 uint32_t L0, uint32_t L1) {
     const uint64_t tb0 = (uint64_t)(t - G.tile_start) * a.tile_blocks;
@@ -91,12 +127,12 @@ __device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupD
 #pragma unroll
         for (int b = 1; b < BPT; ++b) same = same && (!ok[b] || kp[b] == kp[0]);
         if (same) {
-            cipher<NR, DEC, BPT>(s, GlobalKeys{kp[0]}, L0, L1);
+            cipher_rt<DEC, BPT>(s, GlobalKeys{kp[0]}, G.nr, L0, L1);
         } else {
 #pragma unroll
             for (int b = 0; b < BPT; ++b) {
                 if (ok[b])
-                    cipher<NR, DEC, 1>(*reinterpret_cast<uint32_t(*)[1][4]>(&s[b]), GlobalKeys{kp[b]}, L0, L1);
+                    cipher_rt<DEC, 1>(*reinterpret_cast<uint32_t(*)[1][4]>(&s[b]), GlobalKeys{kp[b]}, G.nr, L0, L1);
             }
         }
 #pragma unroll
@@ -172,15 +208,10 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
             int g = 0;
             while (g < kGroups - 1 && t >= lds(gaddr + 32u * g + 4u)) ++g;  // tile_end of group g
             const GroupDev G = load_group(gaddr, g);
-            switch (G.nr * 2 + dir) {
-                case 20: batch_warp_tile<10, false, BPT>(a, G, t, lane, L0, L1); break;
-                case 21: batch_warp_tile<10, true, BPT>(a, G, t, lane, L0, L1); break;
-                case 24: batch_warp_tile<12, false, BPT>(a, G, t, lane, L0, L1); break;
-                case 25: batch_warp_tile<12, true, BPT>(a, G, t, lane, L0, L1); break;
-                case 28: batch_warp_tile<14, false, BPT>(a, G, t, lane, L0, L1); break;
-                case 29: batch_warp_tile<14, true, BPT>(a, G, t, lane, L0, L1); break;
-                default: break;
-            }
+            if (dir)
+                batch_warp_tile<true, BPT>(a, G, t, lane, L0, L1);
+            else
+                batch_warp_tile<false, BPT>(a, G, t, lane, L0, L1);
         }
     }
 }
@@ -376,7 +407,7 @@ aes_batch_plan* aes_batch_plan_create(const aes_msg_desc* msgs, size_t nmsg, con
     }
     P->threads = threads;
     P->bpt = blocks_per_thread;
-    if (build_host_plan(msgs, nmsg, ctxs, nctx, 256u * (uint32_t)blocks_per_thread, true, &P->host)) {
+    if (build_host_plan(msgs, nmsg, ctxs, nctx, 128u * (uint32_t)blocks_per_thread, true, &P->host)) {
         delete P;
         return nullptr;
     }

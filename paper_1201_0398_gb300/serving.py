@@ -52,6 +52,8 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
     srv.close()
     ok = done["status"] == 0
     lat = (done["done_s"] - done["arrival_s"])[ok]
+    wait = (done["launch_s"] - done["arrival_s"])[ok]  # arrival -> its batch's launch
+    service = (done["done_s"] - done["launch_s"])[ok]  # launch -> completion observed
     span = float(done["done_s"].max() - done["arrival_s"].min())
     total = int(w.lengths.sum())
 
@@ -72,6 +74,9 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
         "offered_gbs": total / duration_s / 1e9, "bytes": total,
         "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
         "p999_ms": float(np.percentile(lat, 99.9) * 1e3), "max_ms": float(lat.max() * 1e3),
+        "p50_queue_ms": float(np.percentile(wait, 50) * 1e3), "p99_queue_ms": float(np.percentile(wait, 99) * 1e3),
+        "p50_service_ms": float(np.percentile(service, 50) * 1e3),
+        "p99_service_ms": float(np.percentile(service, 99) * 1e3),
         "mean_batch_msgs": float(n / max(1, len(batches))), "batches": int(stats["batches"]),
         "max_queue": int(stats["max_queue"]), "max_inflight_bytes": int(stats["max_inflight_bytes"]),
         "budget_bytes": int(budget_bytes), "nstreams": nstreams, "shape": f"{threads or 512}x{blocks_per_thread}",
