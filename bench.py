@@ -170,35 +170,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max((r[2] or 0.0) for r in rows)}
 
 
-def dist_setup(n_gpus: int):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch
-        import torch.distributed as dist
+def barrier(ranks):
+    from paper_1201_0398_gb300 import dist
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    return world, rank, local
+    dist.barrier(ranks)
 
 
-def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
+def max_over_ranks(ranks, value: float) -> float:
+    from paper_1201_0398_gb300 import dist
 
-        dist.barrier()
-
-
-def max_over_ranks(world, value: float) -> float:
-    if world == 1:
-        return value
-    import torch
-    import torch.distributed as dist
-
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return dist.max_over_ranks(ranks, value)
 
 
 # ------------------------------------------------------------------ reference arm
@@ -263,7 +244,10 @@ def run_ours(args):
     import paper_1201_0398_gb300 as g
     from paper_1201_0398_gb300 import workloads
 
-    world, rank, local = dist_setup(args.gpus)
+    from paper_1201_0398_gb300 import dist
+
+    ranks = dist.setup()
+    world, rank, local = ranks.world, ranks.rank, ranks.local
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     g.load()
@@ -274,7 +258,7 @@ def run_ours(args):
     keys, x, c, p = {}, {}, {}, {}
     for bits in BITS:
         keys[bits] = g.Key(workloads.random_key(workloads.SEED_BULK[bits], bits))
-        x[bits] = workloads.device_bytes(workloads.SEED_BULK[bits] + 97 * rank, size, device=dev)
+        x[bits] = workloads.device_bytes(dist.shard_seed(workloads.SEED_BULK[bits], ranks), size, device=dev)
         c[bits] = torch.empty_like(x[bits])
         p[bits] = torch.empty_like(x[bits])
     ops = [(bits, dec) for bits in BITS for dec in (False, True)]
@@ -300,7 +284,7 @@ def run_ours(args):
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     props = torch.cuda.get_device_properties(dev)
     with ClockSampler(local) as clocks:
-        barrier(world)
+        barrier(ranks)
         torch.cuda.synchronize()
         start.record(stream)
         for _ in range(args.steps):
@@ -312,9 +296,9 @@ def run_ours(args):
                 ev[op].append((e0, e1))
         end.record(stream)
         torch.cuda.synchronize()
-        barrier(world)
+        barrier(ranks)
     elapsed_s = start.elapsed_time(end) / 1e3
-    elapsed_max = max_over_ranks(world, elapsed_s)
+    elapsed_max = max_over_ranks(ranks, elapsed_s)
     clk = clocks.summary()
     bytes_per_step = len(ops) * size
     value = world * args.steps * bytes_per_step / elapsed_max / 1e9
@@ -374,7 +358,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if not torch.equal(ph, xh[256]):
             raise RuntimeError("e2e round trip failed")
-        barrier(world)
+        barrier(ranks)
         torch.cuda.synchronize()
         s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s2.record(stream)
@@ -382,16 +366,39 @@ def run_ours(args):
             fn()
         e2.record(stream)
         torch.cuda.synchronize()
-        return max_over_ranks(world, s2.elapsed_time(e2) / 1e3)
+        return max_over_ranks(ranks, s2.elapsed_time(e2) / 1e3)
 
     e2e_s = timed_host(e2e_step, e2e_steps)
     zc_s = timed_host(zero_copy_step, e2e_steps)
+
+    def link_probe(kind, reps=5):  # plain torch copies of 1 GiB: what the host link gives
+        side = torch.cuda.Stream(dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            if kind in ("h2d", "both"):
+                x[128].copy_(xh[128], non_blocking=True)
+            if kind in ("d2h", "both"):
+                if kind == "both":
+                    side.wait_stream(stream)
+                    with torch.cuda.stream(side):
+                        ch[128].copy_(x[192], non_blocking=True)
+                    stream.wait_stream(side)
+                else:
+                    ch[128].copy_(x[192], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return reps * size / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+    link = {"h2d_gbs": link_probe("h2d"), "d2h_gbs": link_probe("d2h"), "both_directions_gbs_each": link_probe("both")}
     e2e = {"value": world * e2e_steps * bytes_per_step / e2e_s / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": bytes_per_step, "d2h_bytes_per_step": bytes_per_step, "steps": e2e_steps,
            "path": "aes_pipeline_ecb: pinned host buffers, 64 MiB chunks over 4 device staging slots/streams "
                    "(copy in, table kernel in place, copy out, overlapped)",
            "zero_copy_gbs": world * e2e_steps * bytes_per_step / zc_s / 1e9,
-           "zero_copy_path": "aes_ecb_ex directly on pinned host buffers (kernel loads/stores over the host link)"}
+           "zero_copy_path": "aes_ecb_ex directly on pinned host buffers (kernel loads/stores over the host link)",
+           "link": link}
     del xh, ch, ph, pipe
 
     batched = None
@@ -399,14 +406,14 @@ def run_ours(args):
         for t in (x, c, p):
             t.clear()
         torch.cuda.empty_cache()
-        batched = bench_batched(g, args, stream, world, rank)
+        batched = bench_batched(g, args, stream, ranks)
 
     serving = None
     if not args.no_serving:
         torch.cuda.empty_cache()
         from paper_1201_0398_gb300 import serving as serving_mod
 
-        serving = serving_mod.run(duration_s=args.serve_seconds, seed=workloads.SEED_SERVE + 97 * rank)
+        serving = serving_mod.run(duration_s=args.serve_seconds, seed=dist.shard_seed(workloads.SEED_SERVE, ranks))
         torch.cuda.empty_cache()
 
     cpu = None
@@ -432,13 +439,10 @@ def run_ours(args):
                                                              for k, v in tuned.items()},
             "batched": batched, "serving": serving,
         }), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.destroy_process_group()
+    dist.teardown(ranks)
 
 
-def bench_batched(g, args, stream, world, rank):
+def bench_batched(g, args, stream, ranks):
     """10,000 messages (log-uniform 16 B - 4 MiB, own key each, key sizes 2:1:1,
     mixed directions) in one persistent launch; compared with the same messages
     issued as 10,000 single-message launches."""
@@ -447,12 +451,15 @@ def bench_batched(g, args, stream, world, rank):
 
     from paper_1201_0398_gb300 import autotune, workloads
 
-    w = workloads.batch_workload(seed=workloads.SEED_BATCH + 97 * rank)
+    from paper_1201_0398_gb300 import dist
+
+    world = ranks.world
+    w = workloads.batch_workload(seed=dist.shard_seed(workloads.SEED_BATCH, ranks))
     keys = [g.Key(k) for k in w.keys]
     nblocks = w.lengths // 16
     off = np.concatenate([[0], np.cumsum(w.lengths)[:-1]])
     descs = g.make_descs(off, off, nblocks, np.arange(len(keys)), w.decrypt)
-    x = workloads.device_bytes(workloads.SEED_BATCH + 97 * rank, w.total_bytes, device=torch.device("cuda"))
+    x = workloads.device_bytes(dist.shard_seed(workloads.SEED_BATCH, ranks), w.total_bytes, device=torch.device("cuda"))
     y = torch.empty_like(x)
     plan, report = autotune.tune_batch(descs, keys, x, y)
     plan.launch(x, y, stream=stream)
@@ -465,7 +472,7 @@ def bench_batched(g, args, stream, world, rank):
         raise RuntimeError("batched output differs from the single-message kernel")
 
     def timed(fn, reps):
-        barrier(world)
+        barrier(ranks)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -473,7 +480,7 @@ def bench_batched(g, args, stream, world, rank):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        return max_over_ranks(world, e0.elapsed_time(e1) / 1e3 / reps)
+        return max_over_ranks(ranks, e0.elapsed_time(e1) / 1e3 / reps)
 
     reps = max(3, args.batch_steps)
     t_plan = timed(lambda: plan.launch(x, y, stream=stream), reps)
@@ -539,10 +546,107 @@ def run_sweep(args):
                                   "hbm_frac": 2 * gbs / float(peaks["hbm_gbs"])}), flush=True)
 
 
+class OpenSSLECB:
+    """OpenSSL's EVP AES-ECB from the system libcrypto, used as-is through ctypes
+    (a hardware-accelerated CPU comparison point; absent libraries are skipped)."""
+
+    def __init__(self):
+        import ctypes
+        import ctypes.util
+
+        name = ctypes.util.find_library("crypto")
+        cands = [name] if name else []
+        cands += ["libcrypto.so.3", "libcrypto.so.1.1", "libcrypto.so"]
+        self.lib = None
+        for c in cands:
+            try:
+                self.lib = ctypes.CDLL(c)
+                break
+            except OSError:
+                continue
+        if self.lib is None:
+            raise OSError("libcrypto not found")
+        L, vp = self.lib, ctypes.c_void_p
+        L.EVP_CIPHER_CTX_new.restype = vp
+        L.EVP_CIPHER_CTX_free.argtypes = [vp]
+        for n in ("EVP_aes_128_ecb", "EVP_aes_256_ecb"):
+            getattr(L, n).restype = vp
+        L.EVP_EncryptInit_ex.argtypes = [vp, vp, vp, ctypes.c_char_p, ctypes.c_char_p]
+        L.EVP_CIPHER_CTX_set_padding.argtypes = [vp, ctypes.c_int]
+        L.EVP_EncryptUpdate.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), vp, ctypes.c_int]
+        self.version = None
+        try:
+            L.OpenSSL_version.restype = ctypes.c_char_p
+            self.version = L.OpenSSL_version(0).decode()
+        except AttributeError:
+            pass
+
+    def encrypt(self, key: bytes, bits: int, data, out) -> None:
+        import ctypes
+
+        L = self.lib
+        ctx = L.EVP_CIPHER_CTX_new()
+        cipher = L.EVP_aes_128_ecb() if bits == 128 else L.EVP_aes_256_ecb()
+        L.EVP_EncryptInit_ex(ctx, cipher, None, key, None)
+        L.EVP_CIPHER_CTX_set_padding(ctx, 0)
+        n = ctypes.c_int(0)
+        chunk = 1 << 30
+        for off in range(0, data.size, chunk):
+            m = min(chunk, data.size - off)
+            L.EVP_EncryptUpdate(ctx, ctypes.c_void_p(out.ctypes.data + off), ctypes.byref(n),
+                                ctypes.c_void_p(data.ctypes.data + off), m)
+        L.EVP_CIPHER_CTX_free(ctx)
+
+
+def run_cpu_sweep():
+    """CPU comparison at the paper's Fig. 4 granularity (1, 2, 3, 4 cores and all
+    cores): the oracle and, when present, OpenSSL's EVP AES-ECB; AES-128/256
+    encryption of large buffers; reporting only."""
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    from paper_1201_0398_gb300 import workloads
+
+    allc = os.cpu_count() or 1
+    counts = sorted({1, 2, 3, 4, allc})
+    try:
+        ossl = OpenSSLECB()
+    except OSError:
+        ossl = None
+    for bits in (128, 256):
+        key = workloads.random_key(40 + bits, bits)
+        for n in counts:
+            data = workloads.host_bytes(5, 8 * MiB * n)
+            t0 = time.perf_counter()
+            oracle.ecb(key, bits, data, nthreads=n)
+            dt = time.perf_counter() - t0
+            print(json.dumps({"sweep": "cpu", "impl": "oracle", "bits": bits, "threads": n, "bytes": data.size,
+                              "gbs": data.size / dt / 1e9}), flush=True)
+            if ossl is None:
+                continue
+            per = 128 * MiB
+            data = workloads.host_bytes(6, per * n)
+            out = np.empty_like(data)
+            parts = [(data[i * per:(i + 1) * per], out[i * per:(i + 1) * per]) for i in range(n)]
+            best = None
+            with ThreadPoolExecutor(n) as ex:
+                for _ in range(3):
+                    t0 = time.perf_counter()
+                    list(ex.map(lambda pr: ossl.encrypt(key, bits, pr[0], pr[1]), parts))
+                    dt = time.perf_counter() - t0
+                    best = dt if best is None else min(best, dt)
+            ok = np.array_equal(out[:4096], oracle.ecb(key, bits, data[:4096]))
+            print(json.dumps({"sweep": "cpu", "impl": "openssl-evp", "version": ossl.version, "bits": bits,
+                              "threads": n, "bytes": data.size, "gbs": data.size / best / 1e9,
+                              "matches_oracle": bool(ok)}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.sweep:
         run_sweep(args)
+        run_cpu_sweep()
         return
     if args.impl == "reference":
         run_reference(args)

@@ -10,7 +10,8 @@
 //    field GF((2^4)^2).  A byte a = ah*Y + al with ah, al in GF(2^4) =
 //    GF(2)[z]/(z^4+z+1) and Y^2 = Y + lambda has inverse
 //        a^-1 = (ah * d^-1) Y + ((ah + al) * d^-1),  d = lambda*ah^2 + ah*al + al^2,
-//    and d^-1 = d^14 = d^2 * d^4 * d^8 in GF(2^4).  The change of basis between
+//    and d^-1 in GF(2^4) is four 4-input Boolean functions (3 LOP3 each, truth
+//    tables computed at compile time).  The change of basis between
 //    the AES field and the tower field is a linear map found at compile time
 //    (make_tower below) and merged with the S-box's affine map.  The affine
 //    constant 0x63 is not applied here: it passes unchanged through ShiftRows
@@ -252,6 +253,51 @@ GBAES_HD inline void mul16_lambda(const uint32_t* a, uint32_t* c) {
     mul16(a, l, c);
 }
 
+// Three-input Boolean function given by its truth table LUT (bit (a<<2|b<<1|c)
+// of LUT = f(a,b,c)), applied bitwise: one LOP3 on the device.
+template <int LUT>
+GBAES_HD inline uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+#if defined(__CUDA_ARCH__)
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+#else
+    uint32_t d = 0;
+    for (int k = 0; k < 8; ++k)
+        if ((LUT >> k) & 1)
+            d |= ((k & 4) ? a : ~a) & ((k & 2) ? b : ~b) & ((k & 1) ? c : ~c);
+    return d;
+#endif
+}
+
+// Truth table of output bit I of the GF(16) inverse restricted to input bit 3 = D3,
+// as a function of input bits (0, 1, 2) in LOP3 operand order (a, b, c).
+constexpr int inv16_lut(int I, int D3) {
+    int lut = 0;
+    for (int k = 0; k < 8; ++k) {
+        const int d = ((k >> 2) & 1) | (((k >> 1) & 1) << 1) | ((k & 1) << 2) | (D3 << 3);
+        lut |= ((gf16_inv((uint8_t)d) >> I) & 1) << k;
+    }
+    return lut;
+}
+
+// GF(16) inverse (0 -> 0) of a plane quadruple: each output bit is a
+// four-input function, i.e. two three-input LOP3s selected by d[3] (0xCA:
+// a ? b : c), 12 operations in all.
+GBAES_HD inline void inv16(const uint32_t* d, uint32_t* o) {
+#define GBAES_INV16_BIT(I)                                                   \
+    {                                                                        \
+        const uint32_t lo = lop3<inv16_lut(I, 0)>(d[0], d[1], d[2]);         \
+        const uint32_t hi = lop3<inv16_lut(I, 1)>(d[0], d[1], d[2]);         \
+        o[I] = lop3<0xCA>(d[3], hi, lo);                                     \
+    }
+    GBAES_INV16_BIT(0)
+    GBAES_INV16_BIT(1)
+    GBAES_INV16_BIT(2)
+    GBAES_INV16_BIT(3)
+#undef GBAES_INV16_BIT
+}
+
 // Inverse in GF(2^8) through the tower field, on tower coordinates t[0..7].
 GBAES_HD inline void tower_inv(const uint32_t (&t)[8], uint32_t (&o)[8]) {
     const uint32_t* al = t;
@@ -263,12 +309,8 @@ GBAES_HD inline void tower_inv(const uint32_t (&t)[8], uint32_t (&o)[8]) {
     sq16(al, l2);
 #pragma unroll
     for (int i = 0; i < 4; ++i) d[i] = la2[i] ^ hl[i] ^ l2[i];
-    uint32_t d2[4], d4[4], d8[4], d6[4], di[4];  // d^-1 = d^14 = d^2 d^4 d^8
-    sq16(d, d2);
-    sq16(d2, d4);
-    sq16(d4, d8);
-    mul16(d2, d4, d6);
-    mul16(d6, d8, di);
+    uint32_t di[4];
+    inv16(d, di);
     uint32_t s[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) s[i] = ah[i] ^ al[i];
