@@ -372,21 +372,21 @@ def run_ours(args):
     zc_s = timed_host(zero_copy_step, e2e_steps)
 
     def link_probe(kind, reps=5):  # plain torch copies of 1 GiB: what the host link gives
-        side = torch.cuda.Stream(dev)
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        s_in.wait_stream(stream)
+        s_out.wait_stream(stream)
         for _ in range(reps):
             if kind in ("h2d", "both"):
-                x[128].copy_(xh[128], non_blocking=True)
+                with torch.cuda.stream(s_in):
+                    x[128].copy_(xh[128], non_blocking=True)
             if kind in ("d2h", "both"):
-                if kind == "both":
-                    side.wait_stream(stream)
-                    with torch.cuda.stream(side):
-                        ch[128].copy_(x[192], non_blocking=True)
-                    stream.wait_stream(side)
-                else:
+                with torch.cuda.stream(s_out):
                     ch[128].copy_(x[192], non_blocking=True)
+        stream.wait_stream(s_in)
+        stream.wait_stream(s_out)
         e1.record(stream)
         torch.cuda.synchronize()
         return reps * size / (e0.elapsed_time(e1) / 1e3) / 1e9

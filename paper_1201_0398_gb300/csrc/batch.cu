@@ -45,10 +45,9 @@ __device__ __forceinline__ void cipher_rt(uint32_t (&s)[BPT][4], const KS& ks, i
             s[b][3] ^= k.w;
         }
     }
-    uint4 k = ks.get(1);  // each round's key is fetched one round ahead
 #pragma unroll 1
     for (int r = 1; r < nr; ++r) {
-        const uint4 next = ks.get(r + 1);
+        const uint4 k = ks.get(r);
 #pragma unroll
         for (int b = 0; b < BPT; ++b) {
             if (DECRYPT)
@@ -56,8 +55,8 @@ __device__ __forceinline__ void cipher_rt(uint32_t (&s)[BPT][4], const KS& ks, i
             else
                 enc_round(s[b], L0, L1, k);
         }
-        k = next;
     }
+    const uint4 k = ks.get(nr);
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
         if (DECRYPT)
