@@ -21,7 +21,8 @@
 
 namespace gbaes {
 
-static __constant__ AesTables c_tab = make_aes_tables();
+// Source of the shared-memory fills, read through the read-only global path.
+static __device__ AesTables g_tab = make_aes_tables();
 
 constexpr uint32_t kRegion = 0x10000u;                 // one 64 KiB region: two tables
 constexpr uint32_t kEncBytes = 2 * kRegion;            // T0|T1, T2|T3
@@ -56,19 +57,32 @@ __device__ __forceinline__ uint32_t dynamic_smem_bytes() {
 // 64 KiB-aligned start of the table layout inside the dynamic window.
 __device__ __forceinline__ uint32_t table_base(uint32_t base) { return (base + (kRegion - 1)) & ~(kRegion - 1); }
 
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(addr), "r"(v) : "memory");
+}
+
 // Writes the tables of one direction into shared memory at A (all threads of
-// the CTA take part; the caller synchronises afterwards).
+// the CTA take part; the caller synchronises afterwards).  Pair p = (entry x =
+// p/4, table k = p%4): its 32 lane copies are 128 contiguous bytes at region
+// k/2, slot k%2, written as eight 16-byte stores in an order rotated by p, so
+// the 8 threads of each quarter-warp hit 8 different bank groups.
 __device__ __forceinline__ void fill_tables(uint32_t A, bool decrypt) {
-    const uint32_t* t0 = decrypt ? c_tab.td0 : c_tab.te0;
-    // Region r, slot s, entry x, lane l at word 64x + 32s + l = rotl(T0[x], 8(2r+s)).
-    for (uint32_t w = threadIdx.x; w < (kEncBytes >> 2); w += blockDim.x) {
-        const uint32_t x = (w >> 6) & 255u;
-        const uint32_t rot = 8u * (2u * (w >> 14) + ((w >> 5) & 1u));
-        const uint32_t v = t0[x];
-        sts(A + 4u * w, __funnelshift_l(v, v, rot));
+    const uint32_t* t0 = decrypt ? g_tab.td0 : g_tab.te0;
+    for (uint32_t p = threadIdx.x; p < 1024u; p += blockDim.x) {
+        const uint32_t x = p >> 2, k = p & 3u;
+        const uint32_t v0 = __ldg(t0 + x);
+        const uint32_t v = __funnelshift_l(v0, v0, 8u * k);  // T_k[x] = rotl(T_0[x], 8k)
+        const uint32_t base = A + (k >> 1) * kRegion + x * 256u + (k & 1u) * 128u;
+#pragma unroll
+        for (uint32_t j = 0; j < 8; ++j) sts128(base + 16u * ((j + p) & 7u), v);
     }
     if (decrypt) {
-        for (uint32_t w = threadIdx.x; w < 8192u; w += blockDim.x) sts(A + kSiOffset + 4u * w, c_tab.si4[w >> 5]);
+        for (uint32_t x = threadIdx.x; x < 256u; x += blockDim.x) {
+            const uint32_t v = __ldg(g_tab.si4 + x);
+            const uint32_t base = A + kSiOffset + x * 128u;
+#pragma unroll
+            for (uint32_t j = 0; j < 8; ++j) sts128(base + 16u * ((j + x) & 7u), v);
+        }
     }
 }
 
