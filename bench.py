@@ -63,6 +63,7 @@ def parse_args():
     p.add_argument("--buffer-mib", type=int, default=1024, help="bytes per key size (default 1 GiB)")
     p.add_argument("--e2e-steps", type=int, default=0, help="0 = max(3, steps // 20)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (e2e) leg")
     p.add_argument("--kernel", choices=("table", "bitsliced"), default="table")
     p.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     p.add_argument("--no-batched", action="store_true", help="skip the batched (10,000-message) section")
@@ -84,11 +85,15 @@ def measured_peaks():
 
 
 def kernel_fingerprint() -> str:
+    """Hash of the table kernel's device code (host launcher code excluded)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1201_0398_gb300", "csrc")
     for name in ("ecb_table.cu", "aes_rounds.cuh", "aes_tables.h", "gbaes_internal.h"):
         with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+            text = f.read()
+        if name == "ecb_table.cu":
+            text = text.split(b"// ------------------------------------------------------------------ launcher")[0]
+        h.update(text)
     return h.hexdigest()[:16]
 
 
@@ -206,6 +211,75 @@ def oracle_rate(sample_bytes: int, seed_offset: int = 0):
         if not np.array_equal(pt, data):
             raise RuntimeError("oracle round trip failed")
     return total_b, total_t, threads
+
+
+def run_e2e(g, torch, x, keys, kernel, stream, size, bytes_per_step, e2e_steps, ranks, dev):
+    """The step's workload on pinned host buffers through the host pipeline (and,
+    for comparison, zero copy), host<->device transfers inside the timed region."""
+    xh = {bits: torch.empty(size, dtype=torch.uint8, pin_memory=True) for bits in BITS}
+    ch = {bits: torch.empty(size, dtype=torch.uint8, pin_memory=True) for bits in BITS}
+    ph = torch.empty(size, dtype=torch.uint8, pin_memory=True)
+    for bits in BITS:
+        xh[bits].copy_(x[bits])
+    pipe = g.Pipeline(64 * MiB, 4)
+
+    def e2e_step():
+        for bits in BITS:
+            pipe.ecb(keys[bits], xh[bits], ch[bits], decrypt=False, stream=stream)
+            pipe.ecb(keys[bits], ch[bits], ph, decrypt=True, stream=stream)
+
+    def zero_copy_step():
+        for bits in BITS:
+            g.ecb_ex(keys[bits], xh[bits], ch[bits], decrypt=False, kernel=kernel, stream=stream)
+            g.ecb_ex(keys[bits], ch[bits], ph, decrypt=True, kernel=kernel, stream=stream)
+
+    def timed_host(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        if not torch.equal(ph, xh[256]):
+            raise RuntimeError("e2e round trip failed")
+        barrier(ranks)
+        torch.cuda.synchronize()
+        s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s2.record(stream)
+        for _ in range(reps):
+            fn()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(ranks, s2.elapsed_time(e2) / 1e3)
+
+    e2e_s = timed_host(e2e_step, e2e_steps)
+    zc_s = timed_host(zero_copy_step, e2e_steps)
+
+    def link_probe(kind, reps=5):  # plain torch copies of 1 GiB: what the host link gives
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s_in.wait_stream(stream)
+        s_out.wait_stream(stream)
+        for _ in range(reps):
+            if kind in ("h2d", "both"):
+                with torch.cuda.stream(s_in):
+                    x[128].copy_(xh[128], non_blocking=True)
+            if kind in ("d2h", "both"):
+                with torch.cuda.stream(s_out):
+                    ch[128].copy_(x[192], non_blocking=True)
+        stream.wait_stream(s_in)
+        stream.wait_stream(s_out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return reps * size / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+    link = {"h2d_gbs": link_probe("h2d"), "d2h_gbs": link_probe("d2h"), "both_directions_gbs_each": link_probe("both")}
+    return {"value": ranks.world * e2e_steps * bytes_per_step / e2e_s / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": bytes_per_step, "d2h_bytes_per_step": bytes_per_step, "steps": e2e_steps,
+           "path": "aes_pipeline_ecb: pinned host buffers, 64 MiB chunks over 4 device staging slots/streams "
+                   "(copy in, table kernel in place, copy out, overlapped)",
+           "zero_copy_gbs": ranks.world * e2e_steps * bytes_per_step / zc_s / 1e9,
+           "zero_copy_path": "aes_ecb_ex directly on pinned host buffers (kernel loads/stores over the host link)",
+           "link": link}
+
 
 
 def run_reference(args):
@@ -335,71 +409,10 @@ def run_ours(args):
     }
 
     # ---- e2e: pinned host buffers, copies inside the timed region
-    e2e_steps = args.e2e_steps or max(3, args.steps // 20)
-    xh = {bits: torch.empty(size, dtype=torch.uint8, pin_memory=True) for bits in BITS}
-    ch = {bits: torch.empty(size, dtype=torch.uint8, pin_memory=True) for bits in BITS}
-    ph = torch.empty(size, dtype=torch.uint8, pin_memory=True)
-    for bits in BITS:
-        xh[bits].copy_(x[bits])
-    pipe = g.Pipeline(64 * MiB, 4)
-
-    def e2e_step():
-        for bits in BITS:
-            pipe.ecb(keys[bits], xh[bits], ch[bits], decrypt=False, stream=stream)
-            pipe.ecb(keys[bits], ch[bits], ph, decrypt=True, stream=stream)
-
-    def zero_copy_step():
-        for bits in BITS:
-            g.ecb_ex(keys[bits], xh[bits], ch[bits], decrypt=False, kernel=kernel, stream=stream)
-            g.ecb_ex(keys[bits], ch[bits], ph, decrypt=True, kernel=kernel, stream=stream)
-
-    def timed_host(fn, reps):
-        fn()
-        torch.cuda.synchronize()
-        if not torch.equal(ph, xh[256]):
-            raise RuntimeError("e2e round trip failed")
-        barrier(ranks)
-        torch.cuda.synchronize()
-        s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s2.record(stream)
-        for _ in range(reps):
-            fn()
-        e2.record(stream)
-        torch.cuda.synchronize()
-        return max_over_ranks(ranks, s2.elapsed_time(e2) / 1e3)
-
-    e2e_s = timed_host(e2e_step, e2e_steps)
-    zc_s = timed_host(zero_copy_step, e2e_steps)
-
-    def link_probe(kind, reps=5):  # plain torch copies of 1 GiB: what the host link gives
-        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s_in.wait_stream(stream)
-        s_out.wait_stream(stream)
-        for _ in range(reps):
-            if kind in ("h2d", "both"):
-                with torch.cuda.stream(s_in):
-                    x[128].copy_(xh[128], non_blocking=True)
-            if kind in ("d2h", "both"):
-                with torch.cuda.stream(s_out):
-                    ch[128].copy_(x[192], non_blocking=True)
-        stream.wait_stream(s_in)
-        stream.wait_stream(s_out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return reps * size / (e0.elapsed_time(e1) / 1e3) / 1e9
-
-    link = {"h2d_gbs": link_probe("h2d"), "d2h_gbs": link_probe("d2h"), "both_directions_gbs_each": link_probe("both")}
-    e2e = {"value": world * e2e_steps * bytes_per_step / e2e_s / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": bytes_per_step, "d2h_bytes_per_step": bytes_per_step, "steps": e2e_steps,
-           "path": "aes_pipeline_ecb: pinned host buffers, 64 MiB chunks over 4 device staging slots/streams "
-                   "(copy in, table kernel in place, copy out, overlapped)",
-           "zero_copy_gbs": world * e2e_steps * bytes_per_step / zc_s / 1e9,
-           "zero_copy_path": "aes_ecb_ex directly on pinned host buffers (kernel loads/stores over the host link)",
-           "link": link}
-    del xh, ch, ph, pipe
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(g, torch, x, keys, kernel, stream, size, bytes_per_step,
+                      args.e2e_steps or max(3, args.steps // 20), ranks, dev)
 
     batched = None
     if not args.no_batched:

@@ -90,9 +90,9 @@ static int expand(const uint8_t* key, int bits, uint32_t* enc, uint32_t* dec) {
 static std::mutex g_dev_mu;
 static DeviceInfo g_dev[64];
 static bool g_dev_ok[64];
-typedef CUresult (*PointerAttrFn)(void*, CUpointer_attribute, CUdeviceptr);
-static PointerAttrFn g_ptr_attr = nullptr;
-static bool g_ptr_attr_tried = false;
+typedef CUresult (*PointerAttrsFn)(unsigned int, CUpointer_attribute*, void**, CUdeviceptr);
+static PointerAttrsFn g_ptr_attrs = nullptr;
+static bool g_ptr_attrs_tried = false;
 
 int current_device_info(DeviceInfo* info) {
     int dev = 0;
@@ -114,44 +114,46 @@ int current_device_info(DeviceInfo* info) {
     return AES_OK;
 }
 
-static PointerAttrFn pointer_attr_fn() {
+static PointerAttrsFn pointer_attrs_fn() {
     std::lock_guard<std::mutex> lk(g_dev_mu);
-    if (!g_ptr_attr_tried) {
-        g_ptr_attr_tried = true;
+    if (!g_ptr_attrs_tried) {
+        g_ptr_attrs_tried = true;
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &fn, 12000, cudaEnableDefault, &q) ==
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttributes", &fn, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            g_ptr_attr = (PointerAttrFn)fn;
+            g_ptr_attrs = (PointerAttrsFn)fn;
     }
-    return g_ptr_attr;
+    return g_ptr_attrs;
 }
 
 // Accepts device, managed and page-locked host memory whose allocation holds
 // all of [p, p+bytes); fails closed when the allocation's extent cannot be read.
 // Unregistered pageable host memory is refused even where the GPU could read
-// it, because its extent cannot be checked before the launch.
+// it, because its extent cannot be checked before the launch.  One driver call
+// reads the memory type, the managed flag, the device address and the extent.
 int check_device_range(const void* p, size_t bytes, const char* what) {
     if (!p) return fail(AES_ERR_ARG, "%s is NULL", what);
     if (((uintptr_t)p & 15u) != 0) return fail(AES_ERR_ALIGN, "%s (%p) is not 16-byte aligned", what, p);
-    cudaPointerAttributes attr;
-    cudaError_t e = cudaPointerGetAttributes(&attr, p);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(AES_ERR_ARG, "%s (%p): not a pointer CUDA knows: %s", what, p, cudaGetErrorString(e));
-    }
-    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged && attr.type != cudaMemoryTypeHost)
-        return fail(AES_ERR_ARG, "%s (%p) is not device, managed or page-locked host memory", what, p);
-    if (attr.type == cudaMemoryTypeHost && attr.devicePointer != p)
-        return fail(AES_ERR_ARG, "%s (%p): page-locked memory is not mapped at the same device address", what, p);
-    PointerAttrFn get = pointer_attr_fn();
-    if (!get) return fail(AES_ERR_CUDA, "cuPointerGetAttribute unavailable: cannot check the extent of %s", what);
-    CUdeviceptr start = 0;
+    PointerAttrsFn get = pointer_attrs_fn();
+    if (!get) return fail(AES_ERR_CUDA, "cuPointerGetAttributes unavailable: cannot check the extent of %s", what);
+    unsigned int mem_type = 0, is_managed = 0;
+    CUdeviceptr dev_ptr = 0, start = 0;
     size_t size = 0;
-    if (get(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, (CUdeviceptr)p) != CUDA_SUCCESS ||
-        get(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, (CUdeviceptr)p) != CUDA_SUCCESS)
-        return fail(AES_ERR_ARG, "%s (%p): the extent of its allocation cannot be read", what, p);
+    CUpointer_attribute attrs[5] = {CU_POINTER_ATTRIBUTE_MEMORY_TYPE, CU_POINTER_ATTRIBUTE_IS_MANAGED,
+                                    CU_POINTER_ATTRIBUTE_DEVICE_POINTER, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR,
+                                    CU_POINTER_ATTRIBUTE_RANGE_SIZE};
+    void* data[5] = {&mem_type, &is_managed, &dev_ptr, &start, &size};
+    if (get(5, attrs, data, (CUdeviceptr)p) != CUDA_SUCCESS)
+        return fail(AES_ERR_ARG, "%s (%p): not a pointer CUDA knows", what, p);
+    const bool device = mem_type == CU_MEMORYTYPE_DEVICE || mem_type == CU_MEMORYTYPE_UNIFIED || is_managed;
+    const bool pinned = mem_type == CU_MEMORYTYPE_HOST;
+    if (!device && !pinned)
+        return fail(AES_ERR_ARG, "%s (%p) is not device, managed or page-locked host memory", what, p);
+    if (pinned && dev_ptr != (CUdeviceptr)p)
+        return fail(AES_ERR_ARG, "%s (%p): page-locked memory is not mapped at the same device address", what, p);
+    if (size == 0) return fail(AES_ERR_ARG, "%s (%p): the extent of its allocation cannot be read", what, p);
     const uintptr_t lo = (uintptr_t)p, end = (uintptr_t)start + size;
     if (lo < (uintptr_t)start || lo > end || bytes > end - lo)
         return fail(AES_ERR_ARG, "%s: %zu bytes at %p run past the end of its allocation (%zu bytes left)", what,

@@ -102,6 +102,14 @@ __global__ void __launch_bounds__(1024, 1) table_kernel(const EcbArgs a) {
 
 // ------------------------------------------------------------------ launcher
 
+}  // namespace gbaes
+
+#include <mutex>
+#include <set>
+#include <utility>
+
+namespace gbaes {
+
 namespace {
 
 using KernelFn = void (*)(const EcbArgs);
@@ -146,9 +154,19 @@ int launch_table(const EcbArgs& a, int nr, Mode mode, int threads, int bpt, cuda
     if (rc) return rc;
     // Dynamic shared memory: the whole opt-in limit, so the 64 KiB-aligned
     // layout fits wherever the dynamic window starts (the kernel re-checks).
+    // The attribute is set once per kernel and device.
     const int smem = info.smem_optin;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    cudaError_t e = cudaSuccess;
+    {
+        static std::mutex mu;
+        static std::set<std::pair<KernelFn, int>> done;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!done.count({fn, info.device})) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return fail(AES_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+            done.insert({fn, info.device});
+        }
+    }
     const uint64_t per_cta = (uint64_t)threads * (uint64_t)bpt;
     const uint64_t want = (a.nblocks + per_cta - 1) / per_cta;
     const unsigned grid = (unsigned)(want < (uint64_t)info.sms ? want : (uint64_t)info.sms);
