@@ -66,21 +66,43 @@ __device__ __forceinline__ void cipher_rt(uint32_t (&s)[BPT][4], const KS& ks, i
     }
 }
 
+// Round keys staged in this warp's shared-memory slot (16 B per round).
+struct SmemKeys {
+    uint32_t slot;
+    __device__ __forceinline__ uint4 get(int r) const {
+        uint4 k;
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(k.x), "=r"(k.y), "=r"(k.z), "=r"(k.w)
+                     : "r"(slot + 16u * (uint32_t)r));
+        return k;
+    }
+};
+
 // One warp's tile: tile_blocks consecutive blocks of group G's block space,
 // processed 32*BPT at a time (lane l, slot b -> block base + 32b + l, so every
 // load and store instruction of the warp covers 512 contiguous bytes).
 template <bool DEC, int BPT>
 __device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupDev& G, uint32_t t, uint32_t lane,
-                                                uint32_t L0, uint32_t L1) {
+                                                uint32_t L0, uint32_t L1, uint32_t kslot) {
     const uint64_t tb0 = (uint64_t)(t - G.tile_start) * a.tile_blocks;
     const uint32_t m_lo = a.tile_msg[t];
     const uint32_t m_hi = (t + 1 < G.tile_end) ? a.tile_msg[t + 1] : G.msg_end - 1;
-    // Tiles inside one message (the common case) read its descriptor once.
+    // Tiles inside one message (the common case) read its descriptor once and
+    // stage its schedule in the warp's key slot: one parallel load instead of a
+    // dependent global load per round.  (Every lane has left the previous tile:
+    // the warp met at the tile-index shuffle.)
     uint4 q0 = make_uint4(0, 0, 0, 0), q1 = make_uint4(0, 0, 0, 0);
     if (m_lo == m_hi) {
         const uint4* mp = (const uint4*)(a.msgs + m_lo);
         q0 = __ldg(mp);
         q1 = __ldg(mp + 1);
+        if (lane < (uint32_t)G.nr + 1u) {
+            const uint4 k = __ldg(a.keys + (uint64_t)q1.z * (kSlotWords / 4) + lane);
+            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(kslot + 16u * lane), "r"(k.x), "r"(k.y),
+                         "r"(k.z), "r"(k.w)
+                         : "memory");
+        }
+        __syncwarp();
     }
     for (uint32_t it = 0; it < a.tile_blocks; it += 32u * BPT) {
         uint32_t s[BPT][4];
@@ -126,7 +148,9 @@ __device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupD
         bool same = true;
 #pragma unroll
         for (int b = 1; b < BPT; ++b) same = same && (!ok[b] || kp[b] == kp[0]);
-        if (same) {
+        if (m_lo == m_hi) {
+            cipher_rt<DEC, BPT>(s, SmemKeys{kslot}, G.nr, L0, L1);
+        } else if (same) {
             cipher_rt<DEC, BPT>(s, GlobalKeys{kp[0]}, G.nr, L0, L1);
         } else {
 #pragma unroll
@@ -169,7 +193,8 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
     const uint32_t base = smem_base(smem_raw);
     const uint32_t A = table_base(base);
     const uint32_t gaddr = ((base + dynamic_smem_bytes()) & ~15u) - 32u * kGroups;  // group table
-    if (A + kDecBytes > gaddr) {
+    const uint32_t kslots = A + kDecBytes;                                            // 256 B per warp
+    if (kslots + 256u * 32u > gaddr) {
         if (threadIdx.x == 0) atomicOr(a.status, 2);
         return;
     }
@@ -187,6 +212,7 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t L0 = A | (lane << 2);
     const uint32_t L1 = L0 | 128u;
+    const uint32_t kslot = kslots + 256u * (threadIdx.x >> 5);
     const uint32_t enc_end = lds(gaddr + 32u * 2 + 4u);  // tile_end of group 2
     int cur_dir = -1;
     for (int dir = 0; dir < 2; ++dir) {
@@ -209,9 +235,9 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
             while (g < kGroups - 1 && t >= lds(gaddr + 32u * g + 4u)) ++g;  // tile_end of group g
             const GroupDev G = load_group(gaddr, g);
             if (dir)
-                batch_warp_tile<true, BPT>(a, G, t, lane, L0, L1);
+                batch_warp_tile<true, BPT>(a, G, t, lane, L0, L1, kslot);
             else
-                batch_warp_tile<false, BPT>(a, G, t, lane, L0, L1);
+                batch_warp_tile<false, BPT>(a, G, t, lane, L0, L1, kslot);
         }
     }
 }

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(1024, 1) table_kernel(const EcbArgs a) {
     const uint64_t stride = (uint64_t)gridDim.x * tile;
 
     for (uint64_t t0b = (uint64_t)blockIdx.x * tile; t0b < n; t0b += stride) {
+        if (t0b + threadIdx.x >= n) break;  // no block left for this thread (only the last tile is partial)
         uint32_t s[BPT][4];
         uint4 aux[BPT];  // CTR: data; CBC: previous ciphertext block
         uint64_t idx[BPT];
@@ -167,6 +168,9 @@ int launch_table(const EcbArgs& a, int nr, Mode mode, int threads, int bpt, cuda
             done.insert({fn, info.device});
         }
     }
+    // Small inputs: no more threads than blocks to process (a whole warp at least).
+    const uint64_t need_threads = ((a.nblocks + bpt - 1) / bpt + 31) / 32 * 32;
+    if (need_threads < (uint64_t)threads) threads = (int)(need_threads < 64 ? 64 : need_threads);
     const uint64_t per_cta = (uint64_t)threads * (uint64_t)bpt;
     const uint64_t want = (a.nblocks + per_cta - 1) / per_cta;
     const unsigned grid = (unsigned)(want < (uint64_t)info.sms ? want : (uint64_t)info.sms);
