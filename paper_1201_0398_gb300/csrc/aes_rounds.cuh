@@ -57,31 +57,59 @@ __device__ __forceinline__ uint32_t dynamic_smem_bytes() {
 // 64 KiB-aligned start of the table layout inside the dynamic window.
 __device__ __forceinline__ uint32_t table_base(uint32_t base) { return (base + (kRegion - 1)) & ~(kRegion - 1); }
 
+// Fill store: ordered before the tables' first use by the __syncthreads that
+// follows every fill, so it needs no compiler memory clobber (which would keep
+// the next entry's global load from being issued early).
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t v) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(addr), "r"(v) : "memory");
+    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(addr), "r"(v));
 }
 
 // Writes the tables of one direction into shared memory at A (all threads of
 // the CTA take part; the caller synchronises afterwards).  Pair p = (entry x =
 // p/4, table k = p%4): its 32 lane copies are 128 contiguous bytes at region
 // k/2, slot k%2, written as eight 16-byte stores in an order rotated by p, so
-// the 8 threads of each quarter-warp hit 8 different bank groups.
+// the 8 threads of each quarter-warp hit 8 different bank groups.  A thread
+// loads the entries of up to four pairs before storing any, so small CTAs
+// (many pairs per thread) overlap the global loads.
 __device__ __forceinline__ void fill_tables(uint32_t A, bool decrypt) {
     const uint32_t* t0 = decrypt ? g_tab.td0 : g_tab.te0;
-    for (uint32_t p = threadIdx.x; p < 1024u; p += blockDim.x) {
-        const uint32_t x = p >> 2, k = p & 3u;
-        const uint32_t v0 = __ldg(t0 + x);
-        const uint32_t v = __funnelshift_l(v0, v0, 8u * k);  // T_k[x] = rotl(T_0[x], 8k)
-        const uint32_t base = A + (k >> 1) * kRegion + x * 256u + (k & 1u) * 128u;
+    const uint32_t nt = blockDim.x;
+    for (uint32_t p0 = threadIdx.x; p0 < 1024u; p0 += 4u * nt) {
+        uint32_t v[4];
 #pragma unroll
-        for (uint32_t j = 0; j < 8; ++j) sts128(base + 16u * ((j + p) & 7u), v);
+        for (uint32_t u = 0; u < 4; ++u) {
+            const uint32_t p = p0 + u * nt;
+            v[u] = p < 1024u ? __ldg(t0 + (p >> 2)) : 0u;
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+            const uint32_t p = p0 + u * nt;
+            if (p < 1024u) {
+                const uint32_t k = p & 3u;
+                const uint32_t val = __funnelshift_l(v[u], v[u], 8u * k);  // T_k[x] = rotl(T_0[x], 8k)
+                const uint32_t base = A + (k >> 1) * kRegion + (p >> 2) * 256u + (k & 1u) * 128u;
+#pragma unroll
+                for (uint32_t j = 0; j < 8; ++j) sts128(base + 16u * ((j + p) & 7u), val);
+            }
+        }
     }
     if (decrypt) {
-        for (uint32_t x = threadIdx.x; x < 256u; x += blockDim.x) {
-            const uint32_t v = __ldg(g_tab.si4 + x);
-            const uint32_t base = A + kSiOffset + x * 128u;
+        for (uint32_t x0 = threadIdx.x; x0 < 256u; x0 += 4u * nt) {
+            uint32_t v[4];
 #pragma unroll
-            for (uint32_t j = 0; j < 8; ++j) sts128(base + 16u * ((j + x) & 7u), v);
+            for (uint32_t u = 0; u < 4; ++u) {
+                const uint32_t x = x0 + u * nt;
+                v[u] = x < 256u ? __ldg(g_tab.si4 + x) : 0u;
+            }
+#pragma unroll
+            for (uint32_t u = 0; u < 4; ++u) {
+                const uint32_t x = x0 + u * nt;
+                if (x < 256u) {
+                    const uint32_t base = A + kSiOffset + x * 128u;
+#pragma unroll
+                    for (uint32_t j = 0; j < 8; ++j) sts128(base + 16u * ((j + x) & 7u), v[u]);
+                }
+            }
         }
     }
 }

@@ -193,8 +193,10 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
     const uint32_t base = smem_base(smem_raw);
     const uint32_t A = table_base(base);
     const uint32_t gaddr = ((base + dynamic_smem_bytes()) & ~15u) - 32u * kGroups;  // group table
-    const uint32_t kslots = A + kDecBytes;                                            // 256 B per warp
-    if (kslots + 256u * 32u > gaddr) {
+    // 256 B of key slot per warp: below the 64 KiB-aligned tables when the
+    // dynamic window starts early enough, else above them.
+    const uint32_t kslots = (A >= base + 256u * 32u) ? A - 256u * 32u : A + kDecBytes;
+    if (A + kDecBytes > gaddr || (kslots >= A && kslots + 256u * 32u > gaddr)) {
         if (threadIdx.x == 0) atomicOr(a.status, 2);
         return;
     }
