@@ -102,8 +102,9 @@ int aes_ecb_ex(const aes_ctx* ctx, int decrypt, const void* in, void* out, size_
 
 /* CTR mode (Section 3): out_i = in_i XOR E_K(counter(first_block + i)) for
  * i < nblocks.  iv: HOST pointer to 16 bytes.  counter_kind: AES_CTR_*.  The
- * counter arithmetic is modulo 2^128.  Encryption and decryption are the same
- * call.  in == out allowed. */
+ * counter arithmetic is modulo 2^128; block indices are 64-bit, so
+ * first_block + nblocks - 1 must not exceed 2^64 - 1 (AES_ERR_ARG).  Encryption
+ * and decryption are the same call.  in == out allowed. */
 int aes_ctr_xcrypt(const aes_ctx* ctx, const uint8_t* iv, int counter_kind, uint64_t first_block, const void* in,
                    void* out, size_t nblocks, void* stream);
 

@@ -46,6 +46,17 @@ __device__ __forceinline__ void sts(uint32_t addr, uint32_t v) {
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
+// Streaming 16-byte global load that does not allocate in L1: the input is read
+// once, and keeping it out of L1 keeps its fills out of the SRAM the
+// shared-memory tables live in.
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ uint32_t smem_base(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ uint32_t dynamic_smem_bytes() {

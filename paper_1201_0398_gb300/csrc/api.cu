@@ -314,6 +314,8 @@ int aes_ctr_xcrypt(const aes_ctx* ctx, const uint8_t* iv, int counter_kind, uint
     if (!iv) return fail(AES_ERR_ARG, "iv is NULL");
     if (counter_kind != AES_CTR_BE128 && counter_kind != AES_CTR_LE32_CARRY)
         return fail(AES_ERR_ARG, "unknown counter kind %d", counter_kind);
+    if (nblocks > 0 && first_block > UINT64_MAX - (uint64_t)(nblocks - 1))
+        return fail(AES_ERR_ARG, "first_block + nblocks exceeds 2^64 block indices");
     Tuning t = get_tuning(ctx->bits, 0);
     return run_block_op(ctx, kCtr, in, out, nblocks, AES_KERNEL_TABLE, t.threads, t.bpt, stream, iv, counter_kind,
                         first_block);

@@ -135,7 +135,7 @@ __device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupD
                 const uint64_t in_blk = ((uint64_t)r0.w << 32) | r0.z;
                 const uint64_t out_blk = ((uint64_t)r1.y << 32) | r1.x;
                 const uint64_t off = gb - blk_start;
-                v = __ldcs(a.in + in_blk + off);
+                v = ld_stream(a.in + in_blk + off);
                 oidx[b] = out_blk + off;
                 kp[b] = a.keys + (uint64_t)r1.z * (kSlotWords / 4);
             }

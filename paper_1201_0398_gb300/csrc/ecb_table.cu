@@ -69,10 +69,10 @@ __global__ void __launch_bounds__(1024, 1) table_kernel(const EcbArgs a) {
             uint4 v = make_uint4(0, 0, 0, 0);
             if (MODE == kCtr) {
                 counter_words(a, a.first + idx[b], s[b]);
-                if (ok) v = __ldcs(a.in + idx[b]);
+                if (ok) v = ld_stream(a.in + idx[b]);
                 aux[b] = v;
             } else {
-                if (ok) v = __ldcs(a.in + idx[b]);
+                if (ok) v = ld_stream(a.in + idx[b]);
                 s[b][0] = v.x;
                 s[b][1] = v.y;
                 s[b][2] = v.z;

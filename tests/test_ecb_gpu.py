@@ -243,3 +243,20 @@ def test_bitsliced_equals_table_kernel_large(gbaes):
             a = gbaes.ecb_ex(k, x, decrypt=decrypt, kernel=gbaes.KERNEL_TABLE)
             b = gbaes.ecb_ex(k, x, decrypt=decrypt, kernel=gbaes.KERNEL_BITSLICED)
             assert torch.equal(a, b)
+
+
+def test_ctr_counter_index_limit(gbaes):
+    """Block indices are 64-bit: a call whose last index would pass 2^64 - 1 is
+    refused on the host; one ending exactly at 2^64 - 1 runs, its counters
+    taken as IV + index modulo 2^128 (checked against plain integer arithmetic
+    and ECB of those counter blocks)."""
+    key = bytes(range(16))
+    k = gbaes.Key(key)
+    iv = bytes(16)
+    x = torch.zeros(16 * 4, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gbaes.AesError):
+        gbaes.ctr_xcrypt(k, iv, x, first_block=(1 << 64) - 3)
+    first = (1 << 64) - 4
+    out = host(gbaes.ctr_xcrypt(k, iv, x, first_block=first))
+    ctrs = b"".join((first + i).to_bytes(16, "big") for i in range(4))
+    assert out.tobytes() == oracle.ecb(key, 128, np.frombuffer(ctrs, np.uint8)).tobytes()
