@@ -198,6 +198,10 @@ static int check_ctx(const aes_ctx* ctx) {
 static int check_io(const void* in, const void* out, size_t nblocks, bool allow_inplace) {
     if (nblocks > (SIZE_MAX >> 4)) return fail(AES_ERR_ARG, "nblocks %zu overflows the byte count", nblocks);
     const size_t bytes = nblocks * 16;
+    // Cheap checks on both pointers before any driver query.
+    if (!in) return fail(AES_ERR_ARG, "in is NULL");
+    if (!out) return fail(AES_ERR_ARG, "out is NULL");
+    if (((uintptr_t)in | (uintptr_t)out) & 15u) return fail(AES_ERR_ALIGN, "in and out must be 16-byte aligned");
     int rc = check_device_range(in, bytes, "in");
     if (rc) return rc;
     rc = check_device_range(out, bytes, "out");

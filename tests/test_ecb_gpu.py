@@ -260,3 +260,20 @@ def test_ctr_counter_index_limit(gbaes):
     out = host(gbaes.ctr_xcrypt(k, iv, x, first_block=first))
     ctrs = b"".join((first + i).to_bytes(16, "big") for i in range(4))
     assert out.tobytes() == oracle.ecb(key, 128, np.frombuffer(ctrs, np.uint8)).tobytes()
+
+
+def test_default_kernel_switch(gbaes):
+    """aes_set_kernel changes what aes_encrypt_ecb / aes_decrypt_ecb run; the
+    result is the same bytes either way."""
+    rng = np.random.default_rng(55)
+    key = rng.integers(0, 256, 24, dtype=np.uint8).tobytes()
+    k = gbaes.Key(key)
+    data = rng.integers(0, 256, 16 * 5000, dtype=np.uint8)
+    want = oracle.ecb(key, 192, data)
+    prev = gbaes.set_kernel(gbaes.KERNEL_BITSLICED)
+    try:
+        assert np.array_equal(host(gbaes.encrypt_ecb(k, dev(data))), want)
+        assert np.array_equal(host(gbaes.decrypt_ecb(k, dev(want))), data)
+    finally:
+        gbaes.set_kernel(prev)
+    assert np.array_equal(host(gbaes.encrypt_ecb(k, dev(data))), want)

@@ -98,3 +98,24 @@ def test_kernel_and_tuning_argument_checks(gbaes):
     assert lib.aes_set_tuning(128, 0, 1000, 2) == -1
     assert lib.aes_set_tuning(128, 0, 1024, 3) == -1
     assert lib.aes_set_tuning(128, 0, 1024, 2) == 0
+
+
+def test_argument_checks_before_any_cuda_call(gbaes):
+    """NULL pointers, byte-count overflow and bad flags are refused on the host
+    (no device is touched; these run on a machine without a GPU)."""
+    lib = gbaes.load()
+    k = gbaes.Key(bytes(16))
+    big = ctypes.c_void_p(1 << 20)
+    assert lib.aes_encrypt_ecb(k.handle, None, big, 4, None) == -1  # NULL in
+    assert lib.aes_decrypt_ecb(k.handle, big, None, 4, None) == -1  # NULL out
+    assert lib.aes_encrypt_ecb(k.handle, big, big, (1 << 64) // 16 + 1, None) == -1  # bytes overflow size_t
+    assert lib.aes_encrypt_ecb(None, big, big, 4, None) == -1  # no context
+    assert lib.aes_ecb_ex(k.handle, 2, big, big, 4, 0, 0, 0, None) == -1  # decrypt flag not 0/1
+    assert lib.aes_ecb_ex(k.handle, 0, big, big, 4, 9, 0, 0, None) == -1  # unknown kernel
+    iv = (ctypes.c_uint8 * 16)()
+    assert lib.aes_ctr_xcrypt(k.handle, iv, 5, 0, big, big, 4, None) == -1  # unknown counter kind
+    assert lib.aes_ctr_xcrypt(k.handle, None, 0, 0, big, big, 4, None) == -1  # NULL iv
+    assert lib.aes_cbc_decrypt(k.handle, None, big, big, 4, None) == -1
+    assert lib.aes_ctx_bits(k.handle) == 128 and lib.aes_ctx_bits(None) == -1
+    msg = lib.aes_last_error()
+    assert isinstance(msg, bytes) and len(msg) > 0

@@ -84,6 +84,8 @@ def test_open_loop_replay_and_producer_stop(gbaes):
     srv.drain(10.0)
     done = srv.poll_all()
     assert len(done) == 20_000 and (done["status"] == 0).all()
+    # FIFO admission: nobody waits behind later arrivals for long (no starvation)
+    assert float((done["done_s"] - done["arrival_s"]).max()) < 1.0
     # arrivals are the scheduled times: strictly increasing like the schedule
     order = np.argsort(done["id"])
     arr = done["arrival_s"][order]
