@@ -506,17 +506,6 @@ def bench_batched(g, args, stream, ranks):
 
     t_loop = timed(single_loop, 2)
 
-    # device time of the same messages issued one by one (host launch cost excluded)
-    pairs = []
-    for i in range(len(keys)):
-        a, n = int(off[i]), int(w.lengths[i])
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        g.ecb_ex(keys[i], x[a:a + n], alone[a:a + n], decrypt=bool(w.decrypt[i]), stream=stream)
-        e1.record(stream)
-        pairs.append((e0, e1))
-    torch.cuda.synchronize()
-    t_kernels = sum(e0.elapsed_time(e1) for e0, e1 in pairs) / 1e3
     total = w.total_bytes
     nr_eff = float((w.lengths * np.vectorize(NR.get)(w.bits)).sum() / total)  # lookups per plaintext byte
     peaks, _ = measured_peaks()
@@ -525,7 +514,7 @@ def bench_batched(g, args, stream, ranks):
     return {"value": world * total / t_plan / 1e9, "unit": "GB/s", "messages": len(keys), "bytes": total,
             "ms": 1e3 * t_plan, "graph_gbs": world * total / t_graph / 1e9,
             "single_launch_loop_gbs": world * total / t_loop / 1e9,
-            "single_kernel_sum_gbs": total / t_kernels / 1e9, "shape": report["best"],
+            "shape": report["best"],
             "nr_eff": nr_eff, "smem_roofline_gbs": r_smem, "frac": total / t_plan / 1e9 / r_smem,
             "candidates_ms": report["candidates_ms"], "launches_per_step": 1,
             "workload": "10,000 messages, log-uniform 16 B-4 MiB (x16 B), keys 128/192/256 at 2:1:1, "
