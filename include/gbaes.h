@@ -227,7 +227,7 @@ void aes_pipeline_free(aes_pipeline* pipe);
  * life.  Request data are device pointers owned by the caller, which must keep
  * them valid until the request completes. */
 
-#define AES_SERVER_DRYRUN 1 /* no GPU work: batches complete at the scheduler's next pass */
+#define AES_SERVER_DRYRUN 1 /* no GPU work: a batch completes dryrun_batch_us after its launch */
 
 typedef struct aes_server aes_server;
 
@@ -238,7 +238,7 @@ typedef struct aes_server_config {
     int32_t threads;            /* batched-kernel CTA size (0 = 512) */
     int32_t blocks_per_thread;  /* 1, 2 or 4 (0 = 1) */
     uint32_t max_batch_msgs;    /* requests per batch (0 = 4096) */
-    uint32_t reserved;
+    uint32_t dryrun_batch_us;   /* AES_SERVER_DRYRUN only: simulated time a batch spends "on the GPU" */
     uint64_t max_batch_blocks;  /* blocks per batch, also the largest request (0 = 2^22) */
 } aes_server_config;
 
@@ -296,6 +296,11 @@ int aes_server_poll(aes_server* server, aes_server_completion* out, size_t max);
 
 /* Copies the server's counters. */
 int aes_server_get_stats(aes_server* server, aes_server_stats* out);
+
+/* Cancels request `id` if it is still waiting for admission: it completes at
+ * once with AES_ERR_STATE.  A request already admitted to a batch runs to
+ * completion (its GPU work cannot be withdrawn).  Unknown ids are ignored. */
+int aes_server_cancel(aes_server* server, uint64_t id);
 
 /* Test hook: the batch with this index (0-based, in launch order) fails as if
  * its launch had returned an error; its requests complete with

@@ -117,6 +117,7 @@ def _declare(lib):
         "aes_server_poll": (c.c_int, [vp, vp, sz]),
         "aes_server_get_stats": (c.c_int, [vp, vp]),
         "aes_server_inject_fault": (c.c_int, [vp, c.c_uint64]),
+        "aes_server_cancel": (c.c_int, [vp, c.c_uint64]),
         "aes_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -425,7 +426,7 @@ COMPLETION = np.dtype([("id", "<u8"), ("status", "<i4"), ("batch_msgs", "<u4"), 
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("nstreams", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("blocks_per_thread", ctypes.c_int32), ("max_batch_msgs", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("max_batch_blocks", ctypes.c_uint64)]
+                ("dryrun_batch_us", ctypes.c_uint32), ("max_batch_blocks", ctypes.c_uint64)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -437,11 +438,12 @@ class Server:
     """Continuous-batching server (aes_server) with resident keys."""
 
     def __init__(self, keys, budget_bytes: int = 8 << 30, nstreams: int = 4, threads: int = 0,
-                 blocks_per_thread: int = 0, max_batch_msgs: int = 0, max_batch_blocks: int = 0, dryrun: bool = False):
+                 blocks_per_thread: int = 0, max_batch_msgs: int = 0, max_batch_blocks: int = 0, dryrun: bool = False,
+                 dryrun_batch_us: int = 0):
         self._lib = load()
         self._keys = list(keys)
         cfg = _ServerConfig(int(budget_bytes), int(nstreams), SERVER_DRYRUN if dryrun else 0, int(threads),
-                            int(blocks_per_thread), int(max_batch_msgs), 0, int(max_batch_blocks))
+                            int(blocks_per_thread), int(max_batch_msgs), int(dryrun_batch_us), int(max_batch_blocks))
         h = self._lib.aes_server_create(_ctx_array(self._keys), len(self._keys), ctypes.byref(cfg))
         if not h:
             _check(-1)
@@ -482,6 +484,10 @@ class Server:
         s = _ServerStats()
         _check(self._lib.aes_server_get_stats(self._h, ctypes.byref(s)))
         return {n: getattr(s, n) for n, _ in s._fields_}
+
+    def cancel(self, req_id: int):
+        """Cancels a request still waiting for admission (it completes with AES_ERR_STATE)."""
+        _check(self._lib.aes_server_cancel(self._h, int(req_id)))
 
     def inject_fault(self, batch_index: int):
         _check(self._lib.aes_server_inject_fault(self._h, int(batch_index)))

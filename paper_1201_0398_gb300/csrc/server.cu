@@ -20,14 +20,15 @@
 //  * Latency is completion time minus arrival time (the scheduled arrival for
 //    replays, so a slow server cannot hide queueing delay).
 //
-// A dry-run mode replaces every CUDA call with an immediate completion so the
-// scheduling logic (admission, budget, batching, fault handling, drain) can be
-// exercised on a machine without a GPU.
+// A dry-run mode replaces every CUDA call with a completion after a simulated
+// service time, so the scheduling logic (admission, budget, batching,
+// cancellation, fault handling, drain) can be exercised without a GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -75,7 +76,9 @@ struct aes_server {
     std::chrono::steady_clock::time_point t0;
 
     std::mutex in_mu;
+    std::condition_variable in_cv;  // wakes an idle scheduler
     std::vector<Pending> inbox;
+    std::vector<uint64_t> cancels;  // ids to cancel if still waiting for admission
     std::deque<Pending> queue;  // scheduler thread only
     uint64_t inflight_bytes = 0;  // scheduler thread only
     uint64_t batch_counter = 0;   // scheduler thread only
@@ -184,6 +187,7 @@ static void scheduler_main(aes_server* S) {
     if (!S->dryrun) cudaSetDevice(S->device);
     for (;;) {
         bool worked = false;
+        std::vector<uint64_t> cancels;
         {
             std::lock_guard<std::mutex> lk(S->in_mu);
             if (!S->inbox.empty()) {
@@ -191,12 +195,31 @@ static void scheduler_main(aes_server* S) {
                 S->inbox.clear();
                 worked = true;
             }
+            cancels.swap(S->cancels);
+        }
+        if (!cancels.empty()) {  // only requests not yet admitted can be cancelled
+            std::vector<Pending> gone;
+            for (auto it = S->queue.begin(); it != S->queue.end();) {
+                if (std::find(cancels.begin(), cancels.end(), it->r.id) != cancels.end()) {
+                    gone.push_back(*it);
+                    it = S->queue.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+            if (!gone.empty()) {
+                const double t = S->now();
+                complete(S, gone, AES_ERR_STATE, t, t);
+                worked = true;
+            }
         }
         // Completions.
         for (Slot& slot : S->slots) {
             if (!slot.busy) continue;
             int st = AES_OK;
-            if (!S->dryrun) {
+            if (S->dryrun) {
+                if (S->now() - slot.launch_s < 1e-6 * S->cfg.dryrun_batch_us) continue;
+            } else {
                 cudaError_t q = cudaEventQuery(slot.done);
                 if (q == cudaErrorNotReady) continue;
                 if (q != cudaSuccess) st = AES_ERR_CUDA;
@@ -249,11 +272,17 @@ static void scheduler_main(aes_server* S) {
         if (!worked) {
             bool idle = S->queue.empty();
             for (const Slot& slot : S->slots) idle = idle && !slot.busy;
-            if (idle && S->stop.load()) {
-                std::lock_guard<std::mutex> lk(S->in_mu);
-                if (S->inbox.empty()) break;
+            if (idle) {
+                // Nothing queued or on the GPU: sleep until a submission, a
+                // cancellation or shutdown (bounded, so a missed wake-up costs 1 ms).
+                std::unique_lock<std::mutex> lk(S->in_mu);
+                if (S->inbox.empty() && S->cancels.empty() && S->stop.load()) break;
+                S->in_cv.wait_for(lk, std::chrono::milliseconds(1), [S] {
+                    return !S->inbox.empty() || !S->cancels.empty() || S->stop.load();
+                });
+            } else {
+                std::this_thread::yield();  // batches in flight: poll their events
             }
-            std::this_thread::yield();
         }
     }
 }
@@ -285,8 +314,11 @@ static int enqueue(aes_server* S, const aes_server_request& r, double arrival) {
         std::lock_guard<std::mutex> lk(S->stats_mu);
         S->stats.submitted++;
     }
-    std::lock_guard<std::mutex> lk(S->in_mu);
-    S->inbox.push_back(Pending{r, arrival});
+    {
+        std::lock_guard<std::mutex> lk(S->in_mu);
+        S->inbox.push_back(Pending{r, arrival});
+    }
+    S->in_cv.notify_one();
     return AES_OK;
 }
 
@@ -463,6 +495,16 @@ int aes_server_get_stats(aes_server* S, aes_server_stats* out) {
     return AES_OK;
 }
 
+int aes_server_cancel(aes_server* S, uint64_t id) {
+    if (!S || S->magic != kServerMagic) return fail(AES_ERR_ARG, "invalid aes_server");
+    {
+        std::lock_guard<std::mutex> lk(S->in_mu);
+        S->cancels.push_back(id);
+    }
+    S->in_cv.notify_one();
+    return AES_OK;
+}
+
 int aes_server_inject_fault(aes_server* S, uint64_t batch_index) {
     if (!S || S->magic != kServerMagic) return fail(AES_ERR_ARG, "invalid aes_server");
     S->fault_batch.store(batch_index);
@@ -474,6 +516,7 @@ void aes_server_destroy(aes_server* S) {
     S->producer_stop.store(true);
     if (S->producer.joinable()) S->producer.join();
     S->stop.store(true);
+    S->in_cv.notify_one();
     if (S->scheduler.joinable()) S->scheduler.join();
     S->magic = 0;
     destroy_server(S);

@@ -104,6 +104,38 @@ def test_open_loop_replay_and_producer_stop(gbaes):
     srv.close()
 
 
+def test_cancel_waiting_requests(gbaes):
+    # Budget for one request at a time: later submissions wait for admission
+    # and can be cancelled; the running one cannot.
+    srv = gbaes.Server(keyset(gbaes), budget_bytes=32 * 100, nstreams=1, dryrun=True, dryrun_batch_us=2000)
+    for i in range(200):
+        srv.submit(i, 0, 1 << 20, 2 << 20, 100)
+    for i in range(100, 200):
+        srv.cancel(i)
+    srv.cancel(10_000)  # unknown id: ignored
+    srv.drain(10.0)
+    done = srv.poll_all()
+    assert len(done) == 200
+    st = dict(zip(done["id"].tolist(), done["status"].tolist()))
+    assert all(st[i] == 0 for i in range(50))  # well before the cancels arrived
+    cancelled = [i for i in range(200) if st[i] == -8]
+    assert cancelled and all(i >= 100 for i in cancelled)
+    srv.close()
+
+
+def test_idle_server_sleeps_and_wakes(gbaes):
+    import time
+
+    srv = gbaes.Server(keyset(gbaes), dryrun=True)
+    time.sleep(0.05)  # idle: the scheduler waits on its condition variable
+    t0 = time.perf_counter()
+    srv.submit(1, 0, 1 << 20, 2 << 20, 4)
+    srv.drain(5.0)
+    assert time.perf_counter() - t0 < 0.5
+    assert len(srv.poll_all()) == 1
+    srv.close()
+
+
 def test_server_argument_errors(gbaes):
     srv = gbaes.Server(keyset(gbaes, 2), dryrun=True)
     with pytest.raises(gbaes.AesError):
