@@ -152,10 +152,12 @@ def test_batch_graph_rebase_one_shot_and_in_place(gbaes):
 
 
 @pytest.mark.gpu
-def test_batch_full_workload_10k_messages(gbaes):
+@pytest.mark.parametrize("shape", __import__("paper_1201_0398_gb300.autotune", fromlist=["x"]).BATCH_CANDIDATES)
+def test_batch_full_workload_10k_messages(gbaes, shape):
     """10,000 messages, log-uniform 16 B - 4 MiB, keys 2:1:1 over 128/192/256,
-    mixed directions, one launch; sampled messages against the oracle and every
-    message against the single-message kernel."""
+    mixed directions, one launch, in every plan shape the autotuner may pick for
+    the bench; sampled messages against the oracle and every message against the
+    single-message kernel."""
     w = workloads.batch_workload()
     ks = [gbaes.Key(k) for k in w.keys]
     nblocks = w.lengths // 16
@@ -163,15 +165,15 @@ def test_batch_full_workload_10k_messages(gbaes):
     d = gbaes.make_descs(off, off, nblocks, np.arange(len(ks)), w.decrypt)
     x = workloads.device_bytes(workloads.SEED_BATCH, w.total_bytes)
     y = torch.empty_like(x)
-    plan = gbaes.BatchPlan(d, ks)
+    plan = gbaes.BatchPlan(d, ks, *shape)
     plan.launch(x, y)
     alone = torch.empty_like(x)
     for i in range(len(ks)):
         a, n = int(off[i]), int(w.lengths[i])
         gbaes.ecb_ex(ks[i], x[a:a + n], alone[a:a + n], decrypt=bool(w.decrypt[i]))
     assert torch.equal(alone, y)
-    rng = np.random.default_rng(0)
-    for i in rng.choice(len(ks), 60, replace=False):
+    rng = np.random.default_rng(shape[0] + shape[1])
+    for i in rng.choice(len(ks), 30, replace=False):
         a, n = int(off[i]), int(w.lengths[i])
         take = min(n, 1 << 16)
         src = host(x[a:a + take])

@@ -277,3 +277,20 @@ def test_default_kernel_switch(gbaes):
     finally:
         gbaes.set_kernel(prev)
     assert np.array_equal(host(gbaes.encrypt_ecb(k, dev(data))), want)
+
+
+@pytest.mark.parametrize("shape", __import__("paper_1201_0398_gb300.autotune", fromlist=["x"]).ECB_CANDIDATES)
+def test_one_gib_every_tuner_shape(gbaes, shape):
+    """The 1 GiB single-launch workload in every launch shape the autotuner may
+    pick for the bench: sampled blocks against the oracle, AES-128 encryption and
+    AES-256 decryption (the bench's dominant launch)."""
+    threads, bpt = shape
+    x = workloads.device_bytes(workloads.SEED_BULK[128], workloads.GiB)
+    for bits, dec in ((128, False), (256, True)):
+        key = workloads.random_key(workloads.SEED_BULK[bits], bits)
+        k = gbaes.Key(key)
+        out = gbaes.ecb_ex(k, x, decrypt=dec, threads=threads, blocks_per_thread=bpt)
+        sampled_parity(key, bits, x, out, dec, nsample=1 << 13, seed=threads + bpt)
+        del out
+    del x
+    torch.cuda.empty_cache()
