@@ -383,19 +383,20 @@ GBAES_HD inline void shift_mix_add(uint32_t (&s)[128], const Key& key) {
         const uint32_t* a[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) a[r] = &s[8 * (4 * ((c + r) & 3) + r)];
-        uint32_t u[8];
+        // 2a_r + 3a_{r+1} + a_{r+2} + a_{r+3} = xtime(t_r) + t_{r+1} + a_{r+3},  t_r = a_r + a_{r+1}
+        uint32_t tt[4][8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) u[t] = a[0][t] ^ a[1][t] ^ a[2][t] ^ a[3][t];
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) tt[r][t] = a[r][t] ^ a[(r + 1) & 3][t];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            uint32_t d[8], x2[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) d[t] = a[r][t] ^ a[(r + 1) & 3][t];
-            xtime_planes(d, x2);
+            uint32_t x2[8];
+            xtime_planes(tt[r], x2);
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
                 const int p = 8 * (4 * c + r) + t;
-                n[p] = x2[t] ^ u[t] ^ a[r][t] ^ key(p);  // 2a_r + 3a_{r+1} + a_{r+2} + a_{r+3} + k
+                n[p] = x2[t] ^ tt[(r + 1) & 3][t] ^ a[(r + 3) & 3][t] ^ key(p);
             }
         }
     }
@@ -460,17 +461,17 @@ GBAES_HD inline void add_inv_mix(uint32_t (&s)[128], const Key& key) {
             a[1][t] ^= v4[t];
             a[3][t] ^= v4[t];
         }
-        uint32_t u[8];
+        uint32_t tt[4][8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) u[t] = a[0][t] ^ a[1][t] ^ a[2][t] ^ a[3][t];
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) tt[r][t] = a[r][t] ^ a[(r + 1) & 3][t];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            uint32_t d[8], x2[8];
+            uint32_t x2[8];
+            xtime_planes(tt[r], x2);
 #pragma unroll
-            for (int t = 0; t < 8; ++t) d[t] = a[r][t] ^ a[(r + 1) & 3][t];
-            xtime_planes(d, x2);
-#pragma unroll
-            for (int t = 0; t < 8; ++t) s[8 * (4 * c + r) + t] = x2[t] ^ u[t] ^ a[r][t];
+            for (int t = 0; t < 8; ++t) s[8 * (4 * c + r) + t] = x2[t] ^ tt[(r + 1) & 3][t] ^ a[(r + 3) & 3][t];
         }
     }
 }
