@@ -5,18 +5,22 @@
 // dominates small inputs (Section 3.1; its conclusion advises against small
 // messages).  Here thousands of messages share one launch:
 //
-//  * Host plan.  Messages are grouped by (direction, key size) -- encryption
-//    groups first -- and each group's blocks are numbered contiguously.  The
-//    flattened block space is cut into tiles of threads*BPT blocks; for every
-//    tile the plan records the first message it touches.  Each (key, direction)
+//  * Host plan (batch_plan.h).  Messages are grouped by (direction, key size)
+//    -- encryption groups first -- and each group's blocks are numbered
+//    contiguously.  The flattened block space is cut into tiles; for every tile
+//    the plan records the first message it touches.  Each (key, direction)
 //    gets a slot holding its 4*(Nr+1)-word schedule.  Everything sits in one
 //    device buffer, uploaded once per plan.
-//  * Kernel.  One CTA per SM pulls tile indices from a global atomic counter.
-//    Because encryption tiles come first, a CTA rebuilds its shared-memory
-//    tables (aes_rounds.cuh) at most once, when it first meets a decryption
-//    tile.  Within a tile each block finds its message by binary search over
-//    the tile's message range (no search when the tile lies in one message),
-//    and the rounds read the message's round keys from global memory (L1).
+//  * Kernel.  One CTA per SM holds the shared-memory tables of aes_rounds.cuh.
+//    Each *warp* takes tiles from its direction's atomic counter on its own,
+//    so the dependent loads at the start of one warp's tile overlap the other
+//    warps' lookups; the CTA meets at a barrier only to swap its tables from
+//    the encryption to the decryption set, once.  A block finds its message
+//    by binary search over the tile's message range (none when the tile lies
+//    in one message); a warp whose tile lies in one message stages that
+//    message's schedule in its shared-memory key slot, other tiles read keys
+//    from global memory through L1.  The round count is a run-time loop bound,
+//    so one compact body per direction serves all key sizes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
