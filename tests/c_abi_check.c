@@ -1,0 +1,64 @@
+/* Plain C user of the C ABI (include/gbaes.h): no Python, no torch.
+ * Encrypts and decrypts 1 MiB with each key size through device buffers from
+ * cudaMalloc, checks the round trip and the error codes of bad arguments, and
+ * prints the first ciphertext block of each key size for the test to compare
+ * with the oracle.  Exit status 0 on success. */
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cuda_runtime_api.h>
+
+#include "gbaes.h"
+
+#define CHECK(cond, msg)                                                      \
+    do {                                                                      \
+        if (!(cond)) {                                                        \
+            fprintf(stderr, "FAIL: %s (%s)\n", msg, aes_last_error());        \
+            return 1;                                                         \
+        }                                                                     \
+    } while (0)
+
+int main(void) {
+    const size_t nblocks = 65536, bytes = nblocks * 16;
+    unsigned char* host = (unsigned char*)malloc(bytes);
+    unsigned char* back = (unsigned char*)malloc(bytes);
+    for (size_t i = 0; i < bytes; ++i) host[i] = (unsigned char)(i * 131u + 7u);
+    void *d_in = NULL, *d_out = NULL;
+    CHECK(cudaMalloc(&d_in, bytes) == cudaSuccess && cudaMalloc(&d_out, bytes) == cudaSuccess, "cudaMalloc");
+    cudaStream_t s;
+    CHECK(cudaStreamCreate(&s) == cudaSuccess, "stream");
+    const int sizes[3] = {128, 192, 256};
+    for (int t = 0; t < 3; ++t) {
+        unsigned char key[32];
+        for (int i = 0; i < 32; ++i) key[i] = (unsigned char)(i + 16 * t);
+        aes_ctx* k = aes_expand_key(key, sizes[t]);
+        CHECK(k != NULL && aes_ctx_bits(k) == sizes[t], "aes_expand_key");
+        CHECK(cudaMemcpy(d_in, host, bytes, cudaMemcpyHostToDevice) == cudaSuccess, "copy in");
+        CHECK(aes_encrypt_ecb(k, d_in, d_out, nblocks, s) == AES_OK, "aes_encrypt_ecb");
+        CHECK(aes_decrypt_ecb(k, d_out, d_in, nblocks, s) == AES_OK, "aes_decrypt_ecb");
+        CHECK(cudaStreamSynchronize(s) == cudaSuccess, "sync");
+        CHECK(cudaMemcpy(back, d_in, bytes, cudaMemcpyDeviceToHost) == cudaSuccess, "copy back");
+        CHECK(memcmp(back, host, bytes) == 0, "decrypt(encrypt(x)) != x");
+        unsigned char first[16];
+        CHECK(cudaMemcpy(first, d_out, 16, cudaMemcpyDeviceToHost) == cudaSuccess, "copy first block");
+        printf("%d ", sizes[t]);
+        for (int i = 0; i < 16; ++i) printf("%02x", first[i]);
+        printf("\n");
+        /* bad arguments are error codes, not faults */
+        CHECK(aes_encrypt_ecb(k, (char*)d_in + 1, d_out, 4, s) == AES_ERR_ALIGN, "misaligned in");
+        CHECK(aes_encrypt_ecb(k, d_in, d_out, nblocks + 1, s) == AES_ERR_ARG, "range past the allocation");
+        CHECK(aes_encrypt_ecb(k, host, d_out, 4, s) == AES_ERR_ARG, "pageable host pointer");
+        CHECK(aes_encrypt_ecb(k, d_in, d_out, 0, s) == AES_OK, "empty input");
+        aes_free_ctx(k);
+    }
+    CHECK(aes_expand_key((const unsigned char*)"0123456789abcdef", 100) == NULL, "bad key size");
+    CHECK(aes_device_status(0) == 0, "device status");
+    cudaFree(d_in);
+    cudaFree(d_out);
+    cudaStreamDestroy(s);
+    free(host);
+    free(back);
+    printf("c abi ok\n");
+    return 0;
+}
