@@ -12,10 +12,11 @@
 //    gets a slot holding its 4*(Nr+1)-word schedule.  Everything sits in one
 //    device buffer, uploaded once per plan.
 //  * Kernel.  One CTA per SM holds the shared-memory tables of aes_rounds.cuh.
-//    Each *warp* takes tiles from its direction's atomic counter on its own,
-//    so the dependent loads at the start of one warp's tile overlap the other
-//    warps' lookups; the CTA meets at a barrier only to swap its tables from
-//    the encryption to the decryption set, once.  A block finds its message
+//    Each *warp* starts on a fixed tile, then takes tiles from its
+//    direction's atomic counter on its own, so the dependent loads at the
+//    start of one warp's tile overlap the other warps' lookups; the CTA meets
+//    at a barrier only to swap its tables from the encryption to the
+//    decryption set, once.  A block finds its message
 //    by binary search over the tile's message range (none when the tile lies
 //    in one message); a warp whose tile lies in one message stages that
 //    message's schedule in its shared-memory key slot, other tiles read keys
@@ -27,6 +28,8 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <set>
+#include <utility>
 #include <vector>
 
 #include "aes_rounds.cuh"
@@ -93,20 +96,15 @@ __device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupD
     const uint32_t m_hi = (t + 1 < G.tile_end) ? a.tile_msg[t + 1] : G.msg_end - 1;
     // Tiles inside one message (the common case) read its descriptor once and
     // stage its schedule in the warp's key slot: one parallel load instead of a
-    // dependent global load per round.  (Every lane has left the previous tile:
-    // the warp met at the tile-index shuffle.)
+    // dependent global load per round.  The schedule is loaded and stored only
+    // after the first data loads are issued, so the two loads overlap.  (Every
+    // lane has left the previous tile: the warp met at the tile-index shuffle.)
+    const bool single = m_lo == m_hi;
     uint4 q0 = make_uint4(0, 0, 0, 0), q1 = make_uint4(0, 0, 0, 0);
-    if (m_lo == m_hi) {
+    if (single) {
         const uint4* mp = (const uint4*)(a.msgs + m_lo);
         q0 = __ldg(mp);
         q1 = __ldg(mp + 1);
-        if (lane < (uint32_t)G.nr + 1u) {
-            const uint4 k = __ldg(a.keys + (uint64_t)q1.z * (kSlotWords / 4) + lane);
-            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(kslot + 16u * lane), "r"(k.x), "r"(k.y),
-                         "r"(k.z), "r"(k.w)
-                         : "memory");
-        }
-        __syncwarp();
     }
     for (uint32_t it = 0; it < a.tile_blocks; it += 32u * BPT) {
         uint32_t s[BPT][4];
@@ -148,11 +146,20 @@ __device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupD
             s[b][2] = v.z;
             s[b][3] = v.w;
         }
+        if (single && it == 0) {  // every lane is still here: none has returned yet
+            if (lane < (uint32_t)G.nr + 1u) {
+                const uint4 k = __ldg(a.keys + (uint64_t)q1.z * (kSlotWords / 4) + lane);
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(kslot + 16u * lane), "r"(k.x),
+                             "r"(k.y), "r"(k.z), "r"(k.w)
+                             : "memory");
+            }
+            __syncwarp();
+        }
         if (!ok[0]) return;  // blocks only increase: nothing left in this tile
         bool same = true;
 #pragma unroll
         for (int b = 1; b < BPT; ++b) same = same && (!ok[b] || kp[b] == kp[0]);
-        if (m_lo == m_hi) {
+        if (single) {
             cipher_rt<DEC, BPT>(s, SmemKeys{kslot}, G.nr, L0, L1);
         } else if (same) {
             cipher_rt<DEC, BPT>(s, GlobalKeys{kp[0]}, G.nr, L0, L1);
@@ -186,11 +193,11 @@ __device__ __forceinline__ GroupDev load_group(uint32_t gaddr, int g) {
 }
 
 // Tiles [0, E) are encryption tiles (groups 0-2), [E, ntiles) decryption
-// tiles, with E = tile_end of group 2.  Every warp takes tiles from the
-// direction's own counter until it runs dry, independently of the other
-// warps, so their global-memory latencies overlap.  The CTA meets at a barrier
-// only to swap its shared-memory tables from the encryption to the decryption
-// set, once.
+// tiles, with E = tile_end of group 2.  Every warp starts on a fixed tile,
+// then takes tiles from the direction's own counter until it runs dry,
+// independently of the other warps, so their global-memory latencies overlap.
+// The CTA meets at a barrier only to swap its shared-memory tables from the
+// encryption to the decryption set, once.
 template <int BPT>
 __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -231,10 +238,17 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
             __syncthreads();
             cur_dir = dir;
         }
-        for (;;) {
-            uint32_t t = 0;
-            if (lane == 0) t = atomicAdd(a.counter + dir, 1u);
-            t = __shfl_sync(0xffffffffu, t, 0);
+        // Every warp's first tile is fixed (interleaved over the CTAs, so a
+        // small batch spreads over the SMs); later ones come from the
+        // direction's counter, offset by the number of fixed tiles.
+        const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+        uint32_t t = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+        for (bool first = true;; first = false) {
+            if (!first) {
+                t = 0;
+                if (lane == 0) t = atomicAdd(a.counter + dir, 1u) + nwarps;
+                t = __shfl_sync(0xffffffffu, t, 0);
+            }
             if (t >= t_end - t_begin) break;
             t += t_begin;
             int g = 0;
@@ -298,7 +312,8 @@ int build_host_plan(const aes_msg_desc* d, size_t nmsg, const aes_ctx* const* ct
         G.msg_end = (uint32_t)P->msgs.size();
         G.blocks = blk;
         const uint64_t gt = (blk + tile_blocks - 1) / tile_blocks;
-        if (tiles + gt > 0xFFFFFFF0u) return fail(AES_ERR_ARG, "batch needs too many tiles");
+        // headroom: warps read the counter past the last tile, offset by the fixed first tiles
+        if (tiles + gt > 0xFFFF0000u) return fail(AES_ERR_ARG, "batch needs too many tiles");
         G.tile_start = (uint32_t)tiles;
         G.tile_end = (uint32_t)(tiles + gt);
         // first message of each tile: walk the group's messages once
@@ -388,12 +403,19 @@ static int plan_launch_args(aes_batch_plan* P, const void* in_base, size_t in_by
     return AES_OK;
 }
 
+// The whole opt-in shared memory; the attribute is set once per kernel and device.
 static int batch_smem(BatchKernel fn, int* smem) {
     DeviceInfo info;
     int rc = current_device_info(&info);
     if (rc) return rc;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, info.smem_optin);
-    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    static std::mutex mu;
+    static std::set<std::pair<BatchKernel, int>> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.count({fn, info.device})) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, info.smem_optin);
+        if (e != cudaSuccess) return fail(AES_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        done.insert({fn, info.device});
+    }
     *smem = info.smem_optin;
     return AES_OK;
 }
