@@ -85,27 +85,60 @@ struct SmemKeys {
     }
 };
 
-// One warp's tile: tile_blocks consecutive blocks of group G's block space,
-// processed 32*BPT at a time (lane l, slot b -> block base + 32b + l, so every
-// load and store instruction of the warp covers 512 contiguous bytes).
+// A tile inside one message m (the common case): blocks [tb0, tb0 + n) of the
+// group's block space map to consecutive blocks of m, processed 32*BPT at a
+// time (lane l, slot b -> block it + 32b + l, so every load and store
+// instruction of the warp covers 512 contiguous bytes).  The descriptor is
+// read once and m's schedule is staged in the warp's shared-memory key slot:
+// one parallel load instead of a dependent global load per round, issued once
+// the first data loads are in flight so that the two overlap.  Lanes past the
+// end compute on zeros and store nothing, so the warp stays converged.
 template <bool DEC, int BPT>
-__device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupDev& G, uint32_t t, uint32_t lane,
-                                                uint32_t L0, uint32_t L1, uint32_t kslot) {
-    const uint64_t tb0 = (uint64_t)(t - G.tile_start) * a.tile_blocks;
-    const uint32_t m_lo = a.tile_msg[t];
-    const uint32_t m_hi = (t + 1 < G.tile_end) ? a.tile_msg[t + 1] : G.msg_end - 1;
-    // Tiles inside one message (the common case) read its descriptor once and
-    // stage its schedule in the warp's key slot: one parallel load instead of a
-    // dependent global load per round.  The schedule is loaded and stored only
-    // after the first data loads are issued, so the two loads overlap.  (Every
-    // lane has left the previous tile: the warp met at the tile-index shuffle.)
-    const bool single = m_lo == m_hi;
-    uint4 q0 = make_uint4(0, 0, 0, 0), q1 = make_uint4(0, 0, 0, 0);
-    if (single) {
-        const uint4* mp = (const uint4*)(a.msgs + m_lo);
-        q0 = __ldg(mp);
-        q1 = __ldg(mp + 1);
+__device__ __forceinline__ void single_message_tile(const BatchArgs& a, const GroupDev& G, uint32_t m, uint64_t tb0,
+                                                    uint32_t lane, uint32_t L0, uint32_t L1, uint32_t kslot) {
+    const uint4* mp = (const uint4*)(a.msgs + m);
+    const uint4 q0 = __ldg(mp);
+    const uint4 q1 = __ldg(mp + 1);
+    const uint64_t off = tb0 - (((uint64_t)q0.y << 32) | q0.x);  // tb0 - blk_start
+    const uint4* in = a.in + ((((uint64_t)q0.w << 32) | q0.z) + off);
+    uint4* out = a.out + ((((uint64_t)q1.y << 32) | q1.x) + off);
+    const uint64_t left = G.blocks - tb0;
+    const uint32_t n = left < a.tile_blocks ? (uint32_t)left : a.tile_blocks;
+    for (uint32_t it = 0; it < n; it += 32u * BPT) {
+        uint32_t s[BPT][4];
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const uint32_t i = it + 32u * b + lane;
+            const uint4 v = i < n ? ld_stream(in + i) : make_uint4(0, 0, 0, 0);
+            s[b][0] = v.x;
+            s[b][1] = v.y;
+            s[b][2] = v.z;
+            s[b][3] = v.w;
+        }
+        if (it == 0) {  // (every lane has left the previous tile: the warp met at the tile-index shuffle)
+            if (lane < (uint32_t)G.nr + 1u) {
+                const uint4 k = __ldg(a.keys + (uint64_t)q1.z * (kSlotWords / 4) + lane);
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(kslot + 16u * lane), "r"(k.x),
+                             "r"(k.y), "r"(k.z), "r"(k.w)
+                             : "memory");
+            }
+            __syncwarp();
+        }
+        cipher_rt<DEC, BPT>(s, SmemKeys{kslot}, G.nr, L0, L1);
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const uint32_t i = it + 32u * b + lane;
+            if (i < n) __stcs(out + i, make_uint4(s[b][0], s[b][1], s[b][2], s[b][3]));
+        }
     }
+}
+
+// A tile that crosses message boundaries (messages m_lo..m_hi, m_lo < m_hi):
+// each block finds its message by binary search over that range and reads its
+// round keys from global memory through L1.
+template <bool DEC, int BPT>
+__device__ __forceinline__ void mixed_tile(const BatchArgs& a, const GroupDev& G, uint32_t m_lo, uint32_t m_hi,
+                                           uint64_t tb0, uint32_t lane, uint32_t L0, uint32_t L1) {
     for (uint32_t it = 0; it < a.tile_blocks; it += 32u * BPT) {
         uint32_t s[BPT][4];
         uint64_t oidx[BPT];
@@ -119,20 +152,17 @@ __device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupD
             kp[b] = nullptr;
             oidx[b] = 0;
             if (ok[b]) {
-                uint4 r0 = q0, r1 = q1;
-                if (m_hi != m_lo) {  // largest m in [m_lo, m_hi] with blk_start[m] <= gb
-                    uint32_t lo = m_lo, hi = m_hi;
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi + 1) >> 1;
-                        if (__ldg((const unsigned long long*)(a.msgs + mid)) <= gb)
-                            lo = mid;
-                        else
-                            hi = mid - 1;
-                    }
-                    const uint4* mp = (const uint4*)(a.msgs + lo);
-                    r0 = __ldg(mp);
-                    r1 = __ldg(mp + 1);
+                uint32_t lo = m_lo, hi = m_hi;  // largest m in [m_lo, m_hi] with blk_start[m] <= gb
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (__ldg((const unsigned long long*)(a.msgs + mid)) <= gb)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
                 }
+                const uint4* mp = (const uint4*)(a.msgs + lo);
+                const uint4 r0 = __ldg(mp);
+                const uint4 r1 = __ldg(mp + 1);
                 const uint64_t blk_start = ((uint64_t)r0.y << 32) | r0.x;
                 const uint64_t in_blk = ((uint64_t)r0.w << 32) | r0.z;
                 const uint64_t out_blk = ((uint64_t)r1.y << 32) | r1.x;
@@ -146,22 +176,11 @@ __device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupD
             s[b][2] = v.z;
             s[b][3] = v.w;
         }
-        if (single && it == 0) {  // every lane is still here: none has returned yet
-            if (lane < (uint32_t)G.nr + 1u) {
-                const uint4 k = __ldg(a.keys + (uint64_t)q1.z * (kSlotWords / 4) + lane);
-                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(kslot + 16u * lane), "r"(k.x),
-                             "r"(k.y), "r"(k.z), "r"(k.w)
-                             : "memory");
-            }
-            __syncwarp();
-        }
-        if (!ok[0]) return;  // blocks only increase: nothing left in this tile
+        if (!ok[0]) return;  // blocks only increase: nothing left in this tile for this lane
         bool same = true;
 #pragma unroll
         for (int b = 1; b < BPT; ++b) same = same && (!ok[b] || kp[b] == kp[0]);
-        if (single) {
-            cipher_rt<DEC, BPT>(s, SmemKeys{kslot}, G.nr, L0, L1);
-        } else if (same) {
+        if (same) {
             cipher_rt<DEC, BPT>(s, GlobalKeys{kp[0]}, G.nr, L0, L1);
         } else {
 #pragma unroll
@@ -174,6 +193,20 @@ __device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupD
         for (int b = 0; b < BPT; ++b)
             if (ok[b]) __stcs(a.out + oidx[b], make_uint4(s[b][0], s[b][1], s[b][2], s[b][3]));
     }
+}
+
+// One warp's tile t of group G: tile_blocks consecutive blocks of the group's
+// block space (fewer in the group's last tile).
+template <bool DEC, int BPT>
+__device__ __forceinline__ void batch_warp_tile(const BatchArgs& a, const GroupDev& G, uint32_t t, uint32_t lane,
+                                                uint32_t L0, uint32_t L1, uint32_t kslot) {
+    const uint64_t tb0 = (uint64_t)(t - G.tile_start) * a.tile_blocks;
+    const uint32_t m_lo = a.tile_msg[t];
+    const uint32_t m_hi = (t + 1 < G.tile_end) ? a.tile_msg[t + 1] : G.msg_end - 1;
+    if (m_lo == m_hi)
+        single_message_tile<DEC, BPT>(a, G, m_lo, tb0, lane, L0, L1, kslot);
+    else
+        mixed_tile<DEC, BPT>(a, G, m_lo, m_hi, tb0, lane, L0, L1);
 }
 
 // Group table staged in shared memory (read with a runtime index per tile).

@@ -6,7 +6,7 @@ capture of a launch ends in seconds:
 
   python -m paper_1201_0398_gb300.profile_cases table      # 256 MiB, AES-128 enc + AES-256 dec
   python -m paper_1201_0398_gb300.profile_cases bitsliced  # 64 MiB, AES-128 enc + dec
-  python -m paper_1201_0398_gb300.profile_cases batch      # 2,000 messages, 16 B - 1 MiB (~190 MB)
+  python -m paper_1201_0398_gb300.profile_cases batch      # 10,000 messages, 16 B - 1 MiB (~0.95 GB)
   python -m paper_1201_0398_gb300.profile_cases sweep      # one AES-128 encryption per size, 4 KiB - 1 GiB,
                                                            # table kernel then bitsliced kernel
   python -m paper_1201_0398_gb300.profile_cases singles    # the 10,000-message batch as one batched launch,
@@ -62,7 +62,7 @@ def main(argv=None):
             o, n = int(off[i]), int(w.lengths[i])
             g.ecb_ex(ks[i], x[o:o + n], y[o:o + n], decrypt=bool(w.decrypt[i]))
     else:
-        w = workloads.batch_workload(n=2000, max_len=1 << 20)
+        w = workloads.batch_workload(n=10000, max_len=1 << 20)
         ks = [g.Key(k) for k in w.keys]
         off = np.concatenate([[0], np.cumsum(w.lengths)[:-1]])
         d = g.make_descs(off, off, w.lengths // 16, np.arange(len(ks)), w.decrypt)
