@@ -225,9 +225,27 @@ void aes_pipeline_free(aes_pipeline* pipe);
  * soon as its event fires, freeing budget and slot for requests that arrived
  * meanwhile.  Key schedules stay resident on the device for the server's
  * life.  Request data are device pointers owned by the caller, which must keep
- * them valid until the request completes. */
+ * them valid until the request completes.  AES_SERVER_RESIDENT (below)
+ * replaces the per-batch launches with one kernel that stays on the GPU. */
 
 #define AES_SERVER_DRYRUN 1 /* no GPU work: a batch completes dryrun_batch_us after its launch */
+
+/* Resident mode: instead of one batched-kernel launch per micro-batch, one
+ * kernel stays on the GPU (one CTA per SM) and takes requests as they are
+ * admitted.  The scheduler writes each request as tiles of threads *
+ * blocks_per_thread blocks into a ring in mapped page-locked memory and
+ * publishes them with a release store; a CTA claims a tile, enciphers it, and
+ * the CTA that finishes a request's last tile writes its completion into a
+ * status word in page-locked memory, which the scheduler polls.  No launch,
+ * copy or event per request.  The kernel leaves after resident_idle_us
+ * without work (or resident_lifetime_ms after its launch, or at shutdown) and
+ * is relaunched when work arrives; while it runs it holds every SM, so other
+ * kernels on the device wait for it, and so does a device-wide synchronisation
+ * (cudaDeviceSynchronize).  Request inputs must be complete in
+ * device memory when submitted.  With AES_SERVER_DRYRUN, a host thread runs
+ * the kernel's protocol instead (each tile takes dryrun_batch_us).  Stats:
+ * `batches` counts kernel launches, batch_msgs is 1. */
+#define AES_SERVER_RESIDENT 2
 
 typedef struct aes_server aes_server;
 
@@ -235,11 +253,16 @@ typedef struct aes_server_config {
     uint64_t budget_bytes;      /* in+out bytes in flight (0 = 8 GiB) */
     int32_t nstreams;           /* stream slots, 1..64 (0 = 4) */
     int32_t flags;              /* AES_SERVER_* */
-    int32_t threads;            /* batched-kernel CTA size (0 = 512) */
+    int32_t threads;            /* batched-kernel CTA size (0 = 512; resident mode: 1024) */
     int32_t blocks_per_thread;  /* 1, 2 or 4 (0 = 1) */
     uint32_t max_batch_msgs;    /* requests per batch (0 = 4096) */
     uint32_t dryrun_batch_us;   /* AES_SERVER_DRYRUN only: simulated time a batch spends "on the GPU" */
     uint64_t max_batch_blocks;  /* blocks per batch, also the largest request (0 = 2^22) */
+    uint32_t resident_idle_us;     /* AES_SERVER_RESIDENT: a CTA leaves after this long without work (0 = 2000) */
+    uint32_t resident_lifetime_ms; /* ... and at the latest this long after its launch (0 = 10000) */
+    uint32_t ring_tiles;           /* tile records per direction, a power of two (0 = 65536); must hold the
+                                      largest request */
+    uint32_t ring_items;           /* requests in flight per direction, a power of two (0 = 16384) */
 } aes_server_config;
 
 typedef struct aes_server_request {
@@ -255,7 +278,7 @@ typedef struct aes_server_request {
 typedef struct aes_server_completion {
     uint64_t id;
     int32_t status;      /* AES_OK, or the error the request failed with */
-    uint32_t batch_msgs; /* requests in its batch */
+    uint32_t batch_msgs; /* requests in its batch (1 in resident mode) */
     double arrival_s;    /* arrival (scheduled, for replays) on the server clock, seconds */
     double launch_s;     /* launch of its batch */
     double done_s;       /* when its completion was observed */

@@ -39,6 +39,7 @@ __all__ = [
     "Pipeline",
     "Server",
     "SERVER_DRYRUN",
+    "SERVER_RESIDENT",
     "REQUEST",
     "COMPLETION",
     "KERNEL_TABLE",
@@ -415,6 +416,7 @@ class Pipeline:
 # ------------------------------------------------------------------- serving
 
 SERVER_DRYRUN = 1
+SERVER_RESIDENT = 2
 
 # Match aes_server_request / aes_server_completion (48 and 40 bytes).
 REQUEST = np.dtype([("id", "<u8"), ("in_ptr", "<u8"), ("out_ptr", "<u8"), ("nblocks", "<u8"), ("key_index", "<u4"),
@@ -426,7 +428,9 @@ COMPLETION = np.dtype([("id", "<u8"), ("status", "<i4"), ("batch_msgs", "<u4"), 
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("nstreams", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("blocks_per_thread", ctypes.c_int32), ("max_batch_msgs", ctypes.c_uint32),
-                ("dryrun_batch_us", ctypes.c_uint32), ("max_batch_blocks", ctypes.c_uint64)]
+                ("dryrun_batch_us", ctypes.c_uint32), ("max_batch_blocks", ctypes.c_uint64),
+                ("resident_idle_us", ctypes.c_uint32), ("resident_lifetime_ms", ctypes.c_uint32),
+                ("ring_tiles", ctypes.c_uint32), ("ring_items", ctypes.c_uint32)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -435,15 +439,20 @@ class _ServerStats(ctypes.Structure):
 
 
 class Server:
-    """Continuous-batching server (aes_server) with resident keys."""
+    """Continuous-batching server (aes_server) with resident keys.  resident=True:
+    one kernel stays on the GPU and takes requests from a ring in page-locked
+    memory (AES_SERVER_RESIDENT) instead of one launch per micro-batch."""
 
     def __init__(self, keys, budget_bytes: int = 8 << 30, nstreams: int = 4, threads: int = 0,
                  blocks_per_thread: int = 0, max_batch_msgs: int = 0, max_batch_blocks: int = 0, dryrun: bool = False,
-                 dryrun_batch_us: int = 0):
+                 dryrun_batch_us: int = 0, resident: bool = False, resident_idle_us: int = 0,
+                 resident_lifetime_ms: int = 0, ring_tiles: int = 0, ring_items: int = 0):
         self._lib = load()
         self._keys = list(keys)
-        cfg = _ServerConfig(int(budget_bytes), int(nstreams), SERVER_DRYRUN if dryrun else 0, int(threads),
-                            int(blocks_per_thread), int(max_batch_msgs), int(dryrun_batch_us), int(max_batch_blocks))
+        flags = (SERVER_DRYRUN if dryrun else 0) | (SERVER_RESIDENT if resident else 0)
+        cfg = _ServerConfig(int(budget_bytes), int(nstreams), flags, int(threads), int(blocks_per_thread),
+                            int(max_batch_msgs), int(dryrun_batch_us), int(max_batch_blocks), int(resident_idle_us),
+                            int(resident_lifetime_ms), int(ring_tiles), int(ring_items))
         h = self._lib.aes_server_create(_ctx_array(self._keys), len(self._keys), ctypes.byref(cfg))
         if not h:
             _check(-1)

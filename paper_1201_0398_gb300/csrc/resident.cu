@@ -1,0 +1,234 @@
+// Resident serving kernel.
+//
+// The paper finds the per-operation overhead of each draw dominating small
+// inputs and advises against small messages on the GPU (Section 3.1;
+// Section 4).  The launch-per-batch server (server.cu) amortises launches over
+// micro-batches but still pays a launch, a table upload and an event per
+// batch.  In resident mode the kernel stays on the GPU instead: one CTA per SM
+// holds the shared-memory tables of one direction and takes request tiles as
+// the host publishes them into a ring in page-locked memory, which the GPU
+// reads coherently over the host link (resident.h).  A tile is the CTA's unit
+// of work: up to threads * BPT consecutive blocks of one request, thread i
+// taking blocks i, i + threads, ... so every load and store is coalesced.
+//
+// Thread 0 polls both directions' published-tile counters (its own direction
+// first), claims a tile with a compare-and-swap on the direction's device
+// counter, and copies the tile record into shared memory.  A CTA switches its
+// tables to the other direction when only that direction has work, so every
+// live CTA serves every request.  Every thread fences its stores before the
+// CTA's tile count goes into the request's done counter; the CTA that
+// completes a request resets the counter and writes the request's sequence
+// number to its status word with a system-scope release.
+//
+// Every wait is bounded: a CTA leaves once it has found nothing to claim for
+// idle_ns, once lifetime_ns have passed since its start, or when the host sets
+// the stop word (all three checked between tiles).  Claimed tiles are always
+// finished first, so the host relaunches the kernel whenever it has published
+// work and the kernel has ended.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <set>
+#include <utility>
+
+#include "gbaes_internal.h"
+#include "resident.h"
+#include "rounds_rt.cuh"
+
+namespace gbaes {
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_sys(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint4 ld_volatile_v4(const void* p) {
+    uint4 v;
+    asm volatile("ld.volatile.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p)
+                 : "memory");
+    return v;
+}
+
+// Input load cached in L2 only.  The kernel outlives many requests, whose
+// buffers may be rewritten (by the caller, or by this kernel for in-place
+// requests) while it runs, so neither the read-only path nor L1 may hold them.
+__device__ __forceinline__ uint4 ld_cg(const uint4* p) {
+    uint4 v;
+    asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_release_sys(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void sts_v4(uint32_t addr, uint4 v) {
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint4 lds_v4(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+
+// Thread 0: waits for a tile to claim.  Returns true with the tile's
+// direction and index, or false when the CTA should leave.
+__device__ __forceinline__ bool claim_tile(const ResArgs& a, int dir, uint64_t t_start, int* tdir, uint64_t* tile) {
+    const uint64_t idle_since = globaltimer_ns();
+    for (;;) {
+        const uint64_t now = globaltimer_ns();
+        if (ld_volatile_u32(&a.ctrl->stop) || now - t_start > a.lifetime_ns) return false;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int d = k ? dir ^ 1 : dir;
+            const uint64_t p = ld_acquire_sys(&a.ctrl->pub[d]);
+            unsigned long long c = ld_volatile_u64(&a.claim[d]);
+            while (c < p) {  // each failed swap returns a larger count: at most p - c tries
+                const unsigned long long old = atomicCAS(&a.claim[d], c, c + 1);
+                if (old == c) {
+                    *tdir = d;
+                    *tile = c;
+                    return true;
+                }
+                c = old;
+            }
+        }
+        if (now - idle_since > a.idle_ns) return false;
+        __nanosleep(200);
+    }
+}
+
+template <int BPT>
+__global__ void __launch_bounds__(1024, 1) resident_kernel(const ResArgs a) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const uint32_t base = smem_base(smem_raw);
+    const uint32_t A = table_base(base);
+    const uint32_t end = (base + dynamic_smem_bytes()) & ~15u;
+    // 64-byte control block (the claimed tile's record, a command and its
+    // direction) and a 256-byte key slot: below the tables when the dynamic
+    // window starts early enough, else above them.
+    const uint32_t ctl = (A >= base + 320u) ? A - 320u : A + kDecBytes;
+    const uint32_t kslot = ctl + 64u;
+    if (A + kDecBytes > end || (ctl >= A && ctl + 320u > end)) {
+        if (threadIdx.x == 0) atomicOr(a.err, 4);
+        return;
+    }
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t L0 = A | (lane << 2);
+    const uint32_t L1 = L0 | 128u;
+    int dir = (int)(blockIdx.x & 1u);
+    fill_tables(A, dir != 0);
+    const uint64_t t_start = globaltimer_ns();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int tdir = dir;
+            uint64_t tile = 0;
+            uint32_t cmd = 1;
+            if (claim_tile(a, dir, t_start, &tdir, &tile)) {
+                const uint8_t* rec = (const uint8_t*)(a.tiles + (uint64_t)tdir * a.ring_tiles + (tile & (a.ring_tiles - 1)));
+#pragma unroll
+                for (int q = 0; q < 3; ++q) sts_v4(ctl + 16u * q, ld_volatile_v4(rec + 16 * q));
+                cmd = 0;
+            }
+            sts(ctl + 48u, cmd);
+            sts(ctl + 52u, (uint32_t)tdir);
+        }
+        __syncthreads();  // (also: every thread is done with the previous tile's tables, record and keys)
+        if (lds(ctl + 48u)) break;
+        const int tdir = (int)lds(ctl + 52u);
+        if (tdir != dir) {
+            fill_tables(A, tdir != 0);
+            dir = tdir;
+        }
+        const uint4 r0 = lds_v4(ctl), r1 = lds_v4(ctl + 16u), r2 = lds_v4(ctl + 32u);
+        const uint4* in = (const uint4*)(((uint64_t)r0.y << 32) | r0.x);
+        uint4* out = (uint4*)(((uint64_t)r0.w << 32) | r0.z);
+        const uint32_t n = r2.x, key_slot = r2.y, nr = r2.w;
+        uint32_t s[BPT][4];
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const uint32_t i = threadIdx.x + (uint32_t)b * blockDim.x;
+            const uint4 v = i < n ? ld_cg(in + i) : make_uint4(0, 0, 0, 0);
+            s[b][0] = v.x;
+            s[b][1] = v.y;
+            s[b][2] = v.z;
+            s[b][3] = v.w;
+        }
+        if (threadIdx.x <= nr) sts_v4(kslot + 16u * threadIdx.x, __ldg(a.keys + (uint64_t)key_slot * 16u + threadIdx.x));
+        __syncthreads();  // the tables (after a swap) and the key slot are in place
+        if (dir)
+            cipher_rt<true, BPT>(s, SmemKeys{kslot}, (int)nr, L0, L1);
+        else
+            cipher_rt<false, BPT>(s, SmemKeys{kslot}, (int)nr, L0, L1);
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const uint32_t i = threadIdx.x + (uint32_t)b * blockDim.x;
+            if (i < n) out[i] = make_uint4(s[b][0], s[b][1], s[b][2], s[b][3]);
+        }
+        __threadfence();  // this thread's output before the tile is counted
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint64_t item_blocks = ((uint64_t)r1.y << 32) | r1.x;
+            const uint64_t seq = ((uint64_t)r1.w << 32) | r1.z;
+            const uint64_t slot = (uint64_t)dir * a.ring_items + r2.z;
+            const unsigned long long before = atomicAdd(&a.done[slot], (unsigned long long)n);
+            if (before + n == item_blocks) {  // the request's last tile: every other tile was counted before
+                atomicExch(&a.done[slot], 0ull);
+                __threadfence_system();
+                st_release_sys(&a.status[slot], seq);
+            }
+        }
+    }
+}
+
+using ResidentKernel = void (*)(const ResArgs);
+
+int launch_resident(const ResArgs& a, int threads, int bpt, cudaStream_t stream) {
+    ResidentKernel fn = bpt == 1 ? resident_kernel<1> : bpt == 2 ? resident_kernel<2> : bpt == 4 ? resident_kernel<4> : nullptr;
+    if (!fn) return fail(AES_ERR_ARG, "blocks_per_thread %d: need 1, 2 or 4", bpt);
+    if (threads < 64 || threads > 1024 || threads % 32) return fail(AES_ERR_ARG, "threads %d", threads);
+    DeviceInfo info;
+    int rc = current_device_info(&info);
+    if (rc) return rc;
+    {
+        static std::mutex mu;
+        static std::set<std::pair<ResidentKernel, int>> done;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!done.count({fn, info.device})) {
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, info.smem_optin);
+            if (e != cudaSuccess) return fail(AES_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+            done.insert({fn, info.device});
+        }
+    }
+    fn<<<info.sms, threads, info.smem_optin, stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "resident kernel launch: %s", cudaGetErrorString(e));
+    return AES_OK;
+}
+
+}  // namespace gbaes

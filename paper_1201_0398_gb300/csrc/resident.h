@@ -1,0 +1,57 @@
+// Request ring shared by the server's scheduler thread (server.cu) and the
+// resident serving kernel (resident.cu).
+//
+// The host writes each admitted request as tile records into page-locked
+// memory the GPU reads over the host link, then publishes them by advancing its
+// direction's tile counter (a release store).  CTAs of the resident kernel
+// claim published tiles one at a time from a device-memory counter, encipher
+// them, and count finished blocks per request; the CTA that finishes a
+// request's last block writes the request's sequence number into its status
+// word in page-locked memory, where the scheduler sees it.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gbaes {
+
+// One tile: at most threads * blocks_per_thread consecutive blocks of one request.
+struct ResTile {
+    uint64_t in;           // device address of the tile's first input block
+    uint64_t out;          // device address of its first output block
+    uint64_t item_blocks;  // blocks of the whole request
+    uint64_t seq;          // request number in its direction, from 1
+    uint32_t nblocks;      // blocks in this tile (>= 1)
+    uint32_t key_slot;     // schedule slot in the resident key table (2 * key index + direction)
+    uint32_t item;         // request slot: index of its done counter and status word
+    uint32_t nr;           // rounds: 10, 12 or 14
+};
+static_assert(sizeof(ResTile) == 48, "tile records are three 16-byte words");
+
+struct ResCtrl {
+    uint64_t pub[2];  // tiles published per direction (only grows)
+    uint32_t stop;    // non-zero: every CTA leaves at its next poll
+    uint32_t pad[11];
+};
+static_assert(sizeof(ResCtrl) == 64, "one cache line");
+
+struct ResArgs {
+    const ResTile* tiles;       // [2][ring_tiles], device view of page-locked memory
+    const ResCtrl* ctrl;        // device view of page-locked memory
+    uint64_t* status;           // [2][ring_items], device view of page-locked memory
+    unsigned long long* claim;  // [2] device memory: next tile to claim per direction
+    unsigned long long* done;   // [2][ring_items] device memory: blocks finished per request slot
+    const uint4* keys;          // resident schedules, 256 bytes per slot
+    int* err;                   // the library's device status word
+    uint32_t ring_tiles;        // power of two
+    uint32_t ring_items;        // power of two
+    uint64_t idle_ns;           // a CTA leaves after this long without a tile to claim
+    uint64_t lifetime_ns;       // and, between tiles, once this long has passed since its start
+};
+
+// Launches the resident kernel: one CTA per SM, `threads` threads each,
+// `bpt` (1, 2 or 4) blocks per thread per tile.
+int launch_resident(const ResArgs& a, int threads, int bpt, cudaStream_t stream);
+
+}  // namespace gbaes

@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "batch_plan.h"
+#include "resident.h"
 
 namespace gbaes {
 
@@ -56,6 +57,18 @@ struct Slot {
     double launch_s = 0;
     uint64_t bytes = 0;
     bool busy = false;
+};
+
+// A request published to the resident kernel's ring.
+struct ResItem {
+    Pending p;
+    uint64_t seq;         // request number in its direction, from 1
+    uint32_t slot;        // its done counter and status word
+    uint64_t first_tile;  // its tiles: [first_tile, first_tile + ntiles) of its direction
+    uint64_t ntiles;
+    uint64_t bytes;       // in+out bytes charged to the budget
+    double launch_s;      // when it was published
+    bool done;
 };
 
 }  // namespace gbaes
@@ -99,6 +112,26 @@ struct aes_server {
     std::thread producer;
     std::vector<aes_server_request> replay_reqs;
     double replay_start = 0;
+
+    // Resident mode (scheduler thread only, except where noted).
+    bool resident = false;
+    uint32_t tile_blocks = 0;
+    uint8_t* ring_mem = nullptr;  // page-locked and mapped (plain host memory in a dry run)
+    ResCtrl* rctrl = nullptr;     // host views into ring_mem
+    ResTile* rtiles = nullptr;
+    uint64_t* rstatus = nullptr;
+    ResArgs rargs{};              // device views
+    cudaStream_t rstream = nullptr;
+    uint64_t rpub[2] = {0, 0};        // tiles published per direction
+    uint64_t ritems[2] = {0, 0};      // requests published per direction
+    uint64_t rrel_tiles[2] = {0, 0};  // tiles below this are finished: their ring slots are free
+    uint64_t rrel_items[2] = {0, 0};  // requests up to this sequence number are finished
+    std::deque<ResItem> rinflight[2];
+    bool rlive = false;               // a kernel (or its dry-run stand-in) is running
+    // Dry run: one host thread runs the kernel's claim/record/count/status protocol.
+    std::vector<uint64_t> fake_claim, fake_done;  // stand-in thread only
+    std::thread fake;
+    std::atomic<bool> fake_running{false};
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -183,36 +216,58 @@ static int launch_slot(aes_server* S, Slot& slot) {
     return AES_OK;
 }
 
+// Moves new submissions into the admission queue and completes cancelled
+// requests that are still waiting there.  Returns true if anything changed.
+static bool take_inbox(aes_server* S) {
+    bool worked = false;
+    std::vector<uint64_t> cancels;
+    {
+        std::lock_guard<std::mutex> lk(S->in_mu);
+        if (!S->inbox.empty()) {
+            for (Pending& p : S->inbox) S->queue.push_back(p);
+            S->inbox.clear();
+            worked = true;
+        }
+        cancels.swap(S->cancels);
+    }
+    if (!cancels.empty()) {  // only requests not yet admitted can be cancelled
+        std::vector<Pending> gone;
+        for (auto it = S->queue.begin(); it != S->queue.end();) {
+            if (std::find(cancels.begin(), cancels.end(), it->r.id) != cancels.end()) {
+                gone.push_back(*it);
+                it = S->queue.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        if (!gone.empty()) {
+            const double t = S->now();
+            complete(S, gone, AES_ERR_STATE, t, t);
+            worked = true;
+        }
+    }
+    return worked;
+}
+
+// Sleeps until a submission, a cancellation or shutdown when nothing is queued
+// or in flight (bounded, so a missed wake-up costs 1 ms); yields otherwise.
+// Returns false when the scheduler should exit.
+static bool idle_wait(aes_server* S, bool idle) {
+    if (!idle) {
+        std::this_thread::yield();
+        return true;
+    }
+    std::unique_lock<std::mutex> lk(S->in_mu);
+    if (S->inbox.empty() && S->cancels.empty() && S->stop.load()) return false;
+    S->in_cv.wait_for(lk, std::chrono::milliseconds(1),
+                      [S] { return !S->inbox.empty() || !S->cancels.empty() || S->stop.load(); });
+    return true;
+}
+
 static void scheduler_main(aes_server* S) {
     if (!S->dryrun) cudaSetDevice(S->device);
     for (;;) {
-        bool worked = false;
-        std::vector<uint64_t> cancels;
-        {
-            std::lock_guard<std::mutex> lk(S->in_mu);
-            if (!S->inbox.empty()) {
-                for (Pending& p : S->inbox) S->queue.push_back(p);
-                S->inbox.clear();
-                worked = true;
-            }
-            cancels.swap(S->cancels);
-        }
-        if (!cancels.empty()) {  // only requests not yet admitted can be cancelled
-            std::vector<Pending> gone;
-            for (auto it = S->queue.begin(); it != S->queue.end();) {
-                if (std::find(cancels.begin(), cancels.end(), it->r.id) != cancels.end()) {
-                    gone.push_back(*it);
-                    it = S->queue.erase(it);
-                } else {
-                    ++it;
-                }
-            }
-            if (!gone.empty()) {
-                const double t = S->now();
-                complete(S, gone, AES_ERR_STATE, t, t);
-                worked = true;
-            }
-        }
+        bool worked = take_inbox(S);
         // Completions.
         for (Slot& slot : S->slots) {
             if (!slot.busy) continue;
@@ -272,18 +327,227 @@ static void scheduler_main(aes_server* S) {
         if (!worked) {
             bool idle = S->queue.empty();
             for (const Slot& slot : S->slots) idle = idle && !slot.busy;
-            if (idle) {
-                // Nothing queued or on the GPU: sleep until a submission, a
-                // cancellation or shutdown (bounded, so a missed wake-up costs 1 ms).
-                std::unique_lock<std::mutex> lk(S->in_mu);
-                if (S->inbox.empty() && S->cancels.empty() && S->stop.load()) break;
-                S->in_cv.wait_for(lk, std::chrono::milliseconds(1), [S] {
-                    return !S->inbox.empty() || !S->cancels.empty() || S->stop.load();
-                });
-            } else {
-                std::this_thread::yield();  // batches in flight: poll their events
+            if (!idle_wait(S, idle)) break;  // batches in flight: poll their events
+        }
+    }
+}
+
+// ------------------------------------------------------------ resident mode
+
+// Dry-run stand-in for the resident kernel: one host thread claims published
+// tiles, "enciphers" each for dryrun_batch_us, counts blocks per request and
+// publishes completions, with the kernel's exits (stop word, idle, lifetime).
+static void fake_kernel_main(aes_server* S) {
+    using clock = std::chrono::steady_clock;
+    const clock::time_point start = clock::now();
+    clock::time_point idle_since = start;
+    const uint32_t rt = S->rargs.ring_tiles, ri = S->rargs.ring_items;
+    int dir = 0;
+    for (;;) {
+        const clock::time_point now = clock::now();
+        if (__atomic_load_n(&S->rctrl->stop, __ATOMIC_ACQUIRE) ||
+            (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(now - start).count() > S->rargs.lifetime_ns)
+            break;
+        int tdir = -1;
+        uint64_t tile = 0;
+        for (int k = 0; k < 2 && tdir < 0; ++k) {
+            const int d = k ? dir ^ 1 : dir;
+            const uint64_t pub = __atomic_load_n(&S->rctrl->pub[d], __ATOMIC_ACQUIRE);
+            if (S->fake_claim[d] < pub) {
+                tdir = d;
+                tile = S->fake_claim[d]++;
             }
         }
+        if (tdir < 0) {
+            if ((uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(now - idle_since).count() >
+                S->rargs.idle_ns)
+                break;
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            continue;
+        }
+        dir = tdir;
+        const ResTile R = S->rtiles[(uint64_t)tdir * rt + (tile & (rt - 1))];
+        if (S->cfg.dryrun_batch_us) std::this_thread::sleep_for(std::chrono::microseconds(S->cfg.dryrun_batch_us));
+        uint64_t& done = S->fake_done[(uint64_t)tdir * ri + R.item];
+        done += R.nblocks;
+        if (done == R.item_blocks) {
+            done = 0;
+            __atomic_store_n(&S->rstatus[(uint64_t)tdir * ri + R.item], R.seq, __ATOMIC_RELEASE);
+        }
+        idle_since = clock::now();
+    }
+    S->fake_running.store(false, std::memory_order_release);
+}
+
+// Starts the kernel (or its dry-run stand-in).
+static int start_resident(aes_server* S) {
+    if (S->dryrun) {
+        if (S->fake.joinable()) S->fake.join();  // the previous one has finished
+        S->fake_running.store(true);
+        S->fake = std::thread(fake_kernel_main, S);
+        return AES_OK;
+    }
+    return launch_resident(S->rargs, S->cfg.threads, S->cfg.blocks_per_thread, S->rstream);
+}
+
+// True while the kernel runs; AES_ERR_CUDA in *err if it failed.
+static bool resident_running(aes_server* S, int* err) {
+    *err = AES_OK;
+    if (S->dryrun) return S->fake_running.load(std::memory_order_acquire);
+    const cudaError_t q = cudaStreamQuery(S->rstream);
+    if (q == cudaErrorNotReady) return true;
+    if (q != cudaSuccess) *err = fail(AES_ERR_CUDA, "resident kernel: %s", cudaGetErrorString(q));
+    return false;
+}
+
+// Completes every published, unfinished request with `status` (the kernel has
+// failed or could not start: their work will not be done), frees their ring
+// space and moves the claim counters past their tiles, so that a later kernel
+// starts with the next request.  Called only while no kernel runs.
+static void fail_resident_inflight(aes_server* S, int status) {
+    const double t = S->now();
+    for (int d = 0; d < 2; ++d) {
+        for (ResItem& it : S->rinflight[d]) {
+            if (it.done) continue;
+            std::vector<Pending> one{it.p};
+            S->inflight_bytes -= it.bytes;
+            complete(S, one, status, it.launch_s, t);
+        }
+        if (!S->rinflight[d].empty()) {
+            const ResItem& last = S->rinflight[d].back();
+            S->rrel_tiles[d] = last.first_tile + last.ntiles;
+            S->rrel_items[d] = last.seq;
+            S->rinflight[d].clear();
+        }
+    }
+    if (S->dryrun) {
+        for (int d = 0; d < 2; ++d) S->fake_claim[d] = S->rpub[d];
+        std::fill(S->fake_done.begin(), S->fake_done.end(), 0);
+    } else {
+        unsigned long long claim[2] = {S->rpub[0], S->rpub[1]};
+        cudaMemcpy(S->rargs.claim, claim, sizeof claim, cudaMemcpyHostToDevice);
+        cudaMemset(S->rargs.done, 0, sizeof(unsigned long long) * 2 * S->rargs.ring_items);
+        cudaGetLastError();
+    }
+}
+
+// Writes request p as tile records and publishes them.  Returns false if the
+// direction's ring has no room for it now.
+static bool publish(aes_server* S, const Pending& p, uint64_t bytes) {
+    const int d = (int)p.r.decrypt;
+    const uint32_t rt = S->rargs.ring_tiles, ri = S->rargs.ring_items;
+    const uint64_t tb = S->tile_blocks;
+    const uint64_t ntiles = (p.r.nblocks + tb - 1) / tb;
+    if (S->rpub[d] + ntiles - S->rrel_tiles[d] > rt || S->ritems[d] - S->rrel_items[d] >= ri) return false;
+    const uint64_t seq = ++S->ritems[d];
+    const uint32_t slot = (uint32_t)((seq - 1) & (ri - 1));
+    const aes_ctx& key = S->keys[p.r.key_index];
+    for (uint64_t j = 0; j < ntiles; ++j) {
+        ResTile& R = S->rtiles[(uint64_t)d * rt + ((S->rpub[d] + j) & (rt - 1))];
+        R.in = (uint64_t)(uintptr_t)p.r.in + 16 * tb * j;
+        R.out = (uint64_t)(uintptr_t)p.r.out + 16 * tb * j;
+        R.item_blocks = p.r.nblocks;
+        R.seq = seq;
+        R.nblocks = (uint32_t)std::min<uint64_t>(tb, p.r.nblocks - tb * j);
+        R.key_slot = 2u * p.r.key_index + (uint32_t)d;
+        R.item = slot;
+        R.nr = (uint32_t)key.nr;
+    }
+    ResItem it{p, seq, slot, S->rpub[d], ntiles, bytes, S->now(), false};
+    S->rpub[d] += ntiles;
+    __atomic_store_n(&S->rctrl->pub[d], S->rpub[d], __ATOMIC_RELEASE);  // records before the count
+    S->rinflight[d].push_back(it);
+    return true;
+}
+
+static void scheduler_resident(aes_server* S) {
+    if (!S->dryrun) cudaSetDevice(S->device);
+    for (;;) {
+        bool worked = take_inbox(S);
+        // Completions: status words the kernel wrote.  Ring space is freed in
+        // publication order (a request's tiles and slot are reused only once it
+        // and every request before it in its direction have finished).
+        for (int d = 0; d < 2; ++d) {
+            for (ResItem& it : S->rinflight[d]) {
+                if (it.done) continue;
+                const uint64_t* w = &S->rstatus[(uint64_t)d * S->rargs.ring_items + it.slot];
+                if (__atomic_load_n(w, __ATOMIC_ACQUIRE) != it.seq) continue;
+                it.done = true;
+                S->inflight_bytes -= it.bytes;
+                std::vector<Pending> one{it.p};
+                complete(S, one, AES_OK, it.launch_s, S->now());
+                worked = true;
+            }
+            while (!S->rinflight[d].empty() && S->rinflight[d].front().done) {
+                const ResItem& f = S->rinflight[d].front();
+                S->rrel_tiles[d] = f.first_tile + f.ntiles;
+                S->rrel_items[d] = f.seq;
+                S->rinflight[d].pop_front();
+            }
+        }
+        if (S->rlive) {
+            int err = AES_OK;
+            S->rlive = resident_running(S, &err);
+            if (err != AES_OK) fail_resident_inflight(S, err);
+        }
+        // Admission in arrival order while the budget and the ring have room.
+        while (!S->queue.empty()) {
+            const Pending& p = S->queue.front();
+            const uint64_t b = request_bytes(p.r);
+            if (p.r.nblocks == 0) {
+                std::vector<Pending> one{p};
+                S->queue.pop_front();
+                const double t = S->now();
+                complete(S, one, AES_OK, t, t);
+                worked = true;
+                continue;
+            }
+            if (S->inflight_bytes + b > S->cfg.budget_bytes) break;
+            if (S->batch_counter == S->fault_batch.load()) {
+                ++S->batch_counter;
+                std::vector<Pending> one{p};
+                S->queue.pop_front();
+                const double t = S->now();
+                complete(S, one, fail(AES_ERR_DEVICE, "injected fault"), t, t);
+                worked = true;
+                continue;
+            }
+            if (!publish(S, p, b)) break;
+            ++S->batch_counter;
+            S->inflight_bytes += b;
+            S->queue.pop_front();
+            {
+                std::lock_guard<std::mutex> lk(S->stats_mu);
+                S->stats.max_inflight_bytes = std::max<uint64_t>(S->stats.max_inflight_bytes, S->inflight_bytes);
+                S->stats.max_batch_msgs = 1;
+            }
+            worked = true;
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->stats_mu);
+            S->stats.max_queue = std::max<uint64_t>(S->stats.max_queue, S->queue.size());
+        }
+        const bool inflight = !S->rinflight[0].empty() || !S->rinflight[1].empty();
+        if (inflight && !S->rlive) {  // published work and no kernel: (re)launch
+            const int rc = start_resident(S);
+            {
+                std::lock_guard<std::mutex> lk(S->stats_mu);
+                S->stats.batches++;  // resident mode: kernel launches
+            }
+            if (rc == AES_OK)
+                S->rlive = true;
+            else
+                fail_resident_inflight(S, rc);
+            worked = true;
+        }
+        if (!worked && !idle_wait(S, S->queue.empty() && !inflight)) break;
+    }
+    // Shutdown: everything has completed; ask the kernel to leave and wait for it.
+    __atomic_store_n(&S->rctrl->stop, 1u, __ATOMIC_RELEASE);
+    if (S->dryrun) {
+        if (S->fake.joinable()) S->fake.join();
+    } else if (S->rstream) {
+        cudaStreamSynchronize(S->rstream);
     }
 }
 
@@ -356,7 +620,62 @@ static void destroy_server(aes_server* S) {
         if (slot.host_buf) cudaFreeHost(slot.host_buf);
     }
     if (S->dev_keys) cudaFree(S->dev_keys);
+    if (S->dryrun) {
+        free(S->ring_mem);
+    } else {
+        if (S->ring_mem) cudaFreeHost(S->ring_mem);
+        if (S->rargs.claim) cudaFree(S->rargs.claim);
+        if (S->rargs.done) cudaFree(S->rargs.done);
+        if (S->rstream) cudaStreamDestroy(S->rstream);
+    }
     delete S;
+}
+
+static bool pow2(uint32_t x) { return x && !(x & (x - 1)); }
+
+// Ring memory, counters and the kernel's stream for resident mode.
+static int setup_resident(aes_server* S) {
+    const aes_server_config& c = S->cfg;
+    const uint32_t rt = c.ring_tiles, ri = c.ring_items;
+    const size_t bytes = sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt + sizeof(uint64_t) * 2 * (size_t)ri;
+    uint8_t* dev_view = nullptr;
+    if (S->dryrun) {
+        S->ring_mem = (uint8_t*)aligned_alloc(64, (bytes + 63) & ~(size_t)63);
+        if (!S->ring_mem) return fail(AES_ERR_NOMEM, "out of host memory");
+        dev_view = S->ring_mem;
+        S->fake_claim.assign(2, 0);
+        S->fake_done.assign(2 * (size_t)ri, 0);
+    } else {
+        int can_map = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&can_map, cudaDevAttrCanMapHostMemory, S->device);
+        if (e == cudaSuccess && !can_map) return fail(AES_ERR_CUDA, "resident mode needs mapped page-locked memory");
+        if (e == cudaSuccess) e = cudaHostAlloc(&S->ring_mem, bytes, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&dev_view, S->ring_mem, 0);
+        if (e == cudaSuccess) e = cudaMalloc(&S->rargs.claim, 2 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&S->rargs.done, 2 * (size_t)ri * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemset(S->rargs.claim, 0, 2 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemset(S->rargs.done, 0, 2 * (size_t)ri * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->rstream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? AES_ERR_NOMEM : AES_ERR_CUDA, "resident setup: %s",
+                        cudaGetErrorString(e));
+        }
+    }
+    memset(S->ring_mem, 0, bytes);
+    S->rctrl = (ResCtrl*)S->ring_mem;
+    S->rtiles = (ResTile*)(S->ring_mem + sizeof(ResCtrl));
+    S->rstatus = (uint64_t*)(S->ring_mem + sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt);
+    S->rargs.ctrl = (const ResCtrl*)dev_view;
+    S->rargs.tiles = (const ResTile*)(dev_view + sizeof(ResCtrl));
+    S->rargs.status = (uint64_t*)(dev_view + sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt);
+    S->rargs.keys = S->dev_keys;
+    S->rargs.err = S->status;
+    S->rargs.ring_tiles = rt;
+    S->rargs.ring_items = ri;
+    S->rargs.idle_ns = 1000ull * c.resident_idle_us;
+    S->rargs.lifetime_ns = 1000000ull * c.resident_lifetime_ms;
+    return AES_OK;
 }
 
 }  // namespace gbaes
@@ -369,14 +688,27 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
     if (config) cfg = *config;
     if (cfg.budget_bytes == 0) cfg.budget_bytes = (uint64_t)8 << 30;
     if (cfg.nstreams == 0) cfg.nstreams = 4;
-    if (cfg.threads == 0) cfg.threads = 512;
+    if (cfg.threads == 0) cfg.threads = (cfg.flags & AES_SERVER_RESIDENT) ? 1024 : 512;
     if (cfg.blocks_per_thread == 0) cfg.blocks_per_thread = 1;
     if (cfg.max_batch_msgs == 0) cfg.max_batch_msgs = 4096;
     if (cfg.max_batch_blocks == 0) cfg.max_batch_blocks = (uint64_t)1 << 22;
+    if (cfg.resident_idle_us == 0) cfg.resident_idle_us = 2000;
+    if (cfg.resident_lifetime_ms == 0) cfg.resident_lifetime_ms = 10000;
+    if (cfg.ring_tiles == 0) cfg.ring_tiles = 1u << 16;
+    if (cfg.ring_items == 0) cfg.ring_items = 1u << 14;
     if (cfg.nstreams < 1 || cfg.nstreams > 64 || cfg.threads < 64 || cfg.threads > 1024 || cfg.threads % 32 ||
         (cfg.blocks_per_thread != 1 && cfg.blocks_per_thread != 2 && cfg.blocks_per_thread != 4) ||
-        cfg.max_batch_msgs > (1u << 20)) {
+        cfg.max_batch_msgs > (1u << 20) || (cfg.flags & ~(AES_SERVER_DRYRUN | AES_SERVER_RESIDENT))) {
         fail(AES_ERR_ARG, "invalid server configuration");
+        return nullptr;
+    }
+    const uint64_t res_tile = (uint64_t)cfg.threads * (uint64_t)cfg.blocks_per_thread;
+    if ((cfg.flags & AES_SERVER_RESIDENT) &&
+        (!pow2(cfg.ring_tiles) || !pow2(cfg.ring_items) || cfg.ring_tiles > (1u << 24) || cfg.ring_items > (1u << 24) ||
+         (cfg.max_batch_blocks + res_tile - 1) / res_tile > cfg.ring_tiles)) {
+        fail(AES_ERR_ARG,
+             "resident mode: ring_tiles and ring_items must be powers of two up to 2^24, and ring_tiles must hold "
+             "the largest request (max_batch_blocks / (threads * blocks_per_thread) tiles)");
         return nullptr;
     }
     if (nkeys == 0 || !keys) {
@@ -395,10 +727,12 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
     }
     S->cfg = cfg;
     S->dryrun = (cfg.flags & AES_SERVER_DRYRUN) != 0;
+    S->resident = (cfg.flags & AES_SERVER_RESIDENT) != 0;
+    S->tile_blocks = (uint32_t)res_tile;
     S->keys.assign(nkeys, aes_ctx{});
     for (size_t i = 0; i < nkeys; ++i) S->keys[i] = *keys[i];
     for (size_t i = 0; i < nkeys; ++i) S->key_ptrs.push_back(&S->keys[i]);
-    S->slots.resize(cfg.nstreams);
+    if (!S->resident) S->slots.resize(cfg.nstreams);
     const uint64_t tb = 32ull * cfg.blocks_per_thread;
     S->slot_cap = 256 + (((size_t)cfg.max_batch_msgs * sizeof(MsgDev) + 255) & ~(size_t)255) +
                   4 * (size_t)(cfg.max_batch_blocks / tb + 8) + 4;
@@ -424,10 +758,14 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
             return nullptr;
         }
     }
+    if (S->resident && setup_resident(S) != AES_OK) {
+        destroy_server(S);
+        return nullptr;
+    }
     S->stats.budget_bytes = cfg.budget_bytes;
     S->t0 = std::chrono::steady_clock::now();
     S->magic = kServerMagic;
-    S->scheduler = std::thread(scheduler_main, S);
+    S->scheduler = std::thread(S->resident ? scheduler_resident : scheduler_main, S);
     return S;
 }
 

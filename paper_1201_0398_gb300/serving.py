@@ -17,7 +17,8 @@ GiB = 1 << 30
 
 def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8 << 30, nkeys: int = 1024,
         nstreams: int = 4, threads: int = 0, blocks_per_thread: int = 1, max_batch_msgs: int = 4096,
-        pool_bytes: int = GiB, check_last: int = 1000, seed: int = workloads.SEED_SERVE) -> dict:
+        pool_bytes: int = GiB, check_last: int = 1000, seed: int = workloads.SEED_SERVE,
+        resident: bool = False) -> dict:
     import torch
 
     w = workloads.serve_workload(rate=rate, duration_s=duration_s, nkeys=nkeys, seed=seed)
@@ -42,8 +43,9 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
     reqs["decrypt"] = w.decrypt
     reqs["arrival_s"] = w.arrival_s
 
+    torch.cuda.synchronize()  # inputs complete before the first request
     srv = Server(keys, budget_bytes=budget_bytes, nstreams=nstreams, threads=threads,
-                 blocks_per_thread=blocks_per_thread, max_batch_msgs=max_batch_msgs)
+                 blocks_per_thread=blocks_per_thread, max_batch_msgs=max_batch_msgs, resident=resident)
     srv.replay(reqs)
     srv.replay_join()
     srv.drain(120.0)
@@ -52,7 +54,7 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
     srv.close()
     ok = done["status"] == 0
     lat = (done["done_s"] - done["arrival_s"])[ok]
-    wait = (done["launch_s"] - done["arrival_s"])[ok]  # arrival -> its batch's launch
+    wait = (done["launch_s"] - done["arrival_s"])[ok]  # arrival -> its batch's launch (resident: publication)
     service = (done["done_s"] - done["launch_s"])[ok]  # launch -> completion observed
     span = float(done["done_s"].max() - done["arrival_s"].min())
     total = int(w.lengths.sum())
@@ -70,6 +72,7 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
             mismatches += 1
     batches = np.unique(done["launch_s"])
     return {
+        "mode": "resident kernel" if resident else "launch per micro-batch",
         "value": total / span / 1e9, "unit": "GB/s", "requests": int(n), "completed_ok": int(ok.sum()),
         "offered_gbs": total / duration_s / 1e9, "bytes": total,
         "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
@@ -77,9 +80,10 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
         "p50_queue_ms": float(np.percentile(wait, 50) * 1e3), "p99_queue_ms": float(np.percentile(wait, 99) * 1e3),
         "p50_service_ms": float(np.percentile(service, 50) * 1e3),
         "p99_service_ms": float(np.percentile(service, 99) * 1e3),
-        "mean_batch_msgs": float(n / max(1, len(batches))), "batches": int(stats["batches"]),
+        "mean_batch_msgs": float(n / max(1, len(batches))),
+        ("kernel_launches" if resident else "batches"): int(stats["batches"]),
         "max_queue": int(stats["max_queue"]), "max_inflight_bytes": int(stats["max_inflight_bytes"]),
-        "budget_bytes": int(budget_bytes), "nstreams": nstreams, "shape": f"{threads or 512}x{blocks_per_thread}",
+        "budget_bytes": int(budget_bytes), "nstreams": nstreams, "shape": f"{threads or (1024 if resident else 512)}x{blocks_per_thread}",
         "checked_alone": int(len(idx)), "mismatches": mismatches,
         "workload": f"Poisson {rate:.0f} req/s for {duration_s:g} s, sizes log-uniform 64 B-1 MiB (x16 B), "
                     f"{nkeys} resident keys (128/192/256), encrypt/decrypt 50/50, {budget_bytes >> 30} GiB budget",

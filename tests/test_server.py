@@ -151,6 +151,88 @@ def test_server_argument_errors(gbaes):
         gbaes.Server([], dryrun=True)
 
 
+def test_resident_dryrun_ring_wraps(gbaes):
+    """Resident mode's ring protocol (the kernel's stand-in is a host thread):
+    a ring of 64 tile records and 16 request slots per direction serves 3,000
+    requests of 1-300 blocks (64-block tiles), so records and slots are reused
+    many times; every request completes once, in budget."""
+    rng = np.random.default_rng(11)
+    srv = gbaes.Server(keyset(gbaes), budget_bytes=1 << 20, dryrun=True, resident=True, threads=64,
+                       blocks_per_thread=1, ring_tiles=64, ring_items=16, max_batch_blocks=4096)
+    reqs = fake_requests(gbaes, 3000, rng, max_blocks=300)
+    for r in reqs:
+        srv.submit(int(r["id"]), int(r["key_index"]), int(r["in_ptr"]), int(r["out_ptr"]), int(r["nblocks"]),
+                   bool(r["decrypt"]))
+    srv.drain(30.0)
+    done = srv.poll_all()
+    st = srv.stats()
+    srv.close()
+    assert sorted(done["id"].tolist()) == list(range(3000))
+    assert (done["status"] == 0).all() and (done["batch_msgs"] == 1).all()
+    assert st["completed"] == 3000 and st["failed"] == 0 and st["max_inflight_bytes"] <= 1 << 20
+    assert st["batches"] >= 1  # kernel launches
+    assert (done["done_s"] >= done["launch_s"]).all() and (done["launch_s"] >= done["arrival_s"]).all()
+
+
+def test_resident_dryrun_idle_exit_and_relaunch(gbaes):
+    """The kernel leaves after resident_idle_us without work; the next request
+    relaunches it.  A short lifetime under steady load also ends kernels that
+    are busy, and the scheduler relaunches them with nothing lost."""
+    import time
+
+    srv = gbaes.Server(keyset(gbaes), dryrun=True, resident=True, resident_idle_us=500)
+    for i in range(10):
+        srv.submit(i, i % 4, 1 << 20, 2 << 20, 8, bool(i & 1))
+    srv.drain(10.0)
+    time.sleep(0.03)  # well past the idle limit: the stand-in kernel has left
+    for i in range(10, 20):
+        srv.submit(i, i % 4, 1 << 20, 2 << 20, 8, bool(i & 1))
+    srv.drain(10.0)
+    assert len(srv.poll_all()) == 20
+    assert srv.stats()["batches"] >= 2
+    srv.close()
+
+    rng = np.random.default_rng(12)
+    srv = gbaes.Server(keyset(gbaes), dryrun=True, resident=True, resident_lifetime_ms=5)
+    srv.replay(fake_requests(gbaes, 5000, rng, rate=50_000.0))  # ~0.1 s of arrivals
+    srv.replay_join()
+    srv.drain(10.0)
+    done = srv.poll_all()
+    assert len(done) == 5000 and (done["status"] == 0).all()
+    assert srv.stats()["batches"] >= 5
+    srv.close()
+
+
+def test_resident_config_errors(gbaes):
+    with pytest.raises(gbaes.AesError):  # not a power of two
+        gbaes.Server(keyset(gbaes), dryrun=True, resident=True, ring_tiles=100)
+    with pytest.raises(gbaes.AesError):  # the largest request (2^22 blocks) needs 8,192 tiles of 512
+        gbaes.Server(keyset(gbaes), dryrun=True, resident=True, ring_tiles=4096)
+    srv = gbaes.Server(keyset(gbaes), dryrun=True, resident=True, ring_tiles=4096, max_batch_blocks=4096 * 512)
+    srv.close()
+
+
+def test_resident_dryrun_fault_cancel_budget(gbaes):
+    """An injected fault fails one request; requests still waiting for admission
+    (the budget admits one at a time) can be cancelled; the rest complete."""
+    srv = gbaes.Server(keyset(gbaes), budget_bytes=32 * 100, dryrun=True, resident=True, dryrun_batch_us=2000,
+                       threads=64, blocks_per_thread=1)
+    srv.inject_fault(3)
+    for i in range(60):
+        srv.submit(i, 0, 1 << 20, 2 << 20, 100)
+    for i in range(40, 60):
+        srv.cancel(i)
+    srv.drain(30.0)
+    done = srv.poll_all()
+    st = dict(zip(done["id"].tolist(), done["status"].tolist()))
+    assert len(st) == 60
+    assert st[3] == -7 and sum(v == -7 for v in st.values()) == 1
+    assert all(st[i] == 0 for i in range(10) if i != 3)
+    assert any(st[i] == -8 for i in range(40, 60))
+    assert srv.stats()["max_inflight_bytes"] <= 32 * 100
+    srv.close()
+
+
 # ------------------------------------------------------------------------- GPU
 
 torch = pytest.importorskip("torch")
@@ -230,3 +312,109 @@ def test_server_batches_overlap_on_device(gbaes):
     # some batch is launched while an earlier one is still running
     overlapping = sum(int(np.any((starts < e) & (starts > s))) for s, e in batches)
     assert overlapping > 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("threads,bpt,ring_tiles,ring_items", [(512, 1, 0, 0), (256, 2, 256, 64), (1024, 4, 64, 16)])
+def test_resident_results_equal_alone_and_oracle(gbaes, threads, bpt, ring_tiles, ring_items):
+    """Resident mode: 4,000 requests (64 B - 256 KiB, 64 keys of all sizes, both
+    directions) at 100k req/s through one kernel that stays on the GPU; small
+    rings in two cases so tile records and request slots are reused."""
+    rng = np.random.default_rng(threads + bpt)
+    nkeys = 64
+    bits = rng.choice([128, 192, 256], nkeys)
+    raw_keys = [rng.integers(0, 256, b // 8, dtype=np.uint8).tobytes() for b in bits]
+    keys = [gbaes.Key(k) for k in raw_keys]
+    reqs, x, y, in_off, out_off, lengths = device_requests(gbaes, rng, 4000, bits, 8 << 20, 256 << 10, 100_000.0)
+    torch.cuda.synchronize()
+    max_blocks = (ring_tiles or 1 << 16) * threads * bpt
+    srv = gbaes.Server(keys, resident=True, threads=threads, blocks_per_thread=bpt, ring_tiles=ring_tiles,
+                       ring_items=ring_items, max_batch_blocks=min(max_blocks, 1 << 22))
+    srv.replay(reqs)
+    srv.replay_join()
+    srv.drain(60.0)
+    done = srv.poll_all()
+    st = srv.stats()
+    srv.close()
+    assert len(done) == len(reqs) and (done["status"] == 0).all()
+    assert st["batches"] >= 1
+    alone = torch.zeros_like(y)
+    for i in range(len(reqs)):
+        a, b, n = int(in_off[i]), int(out_off[i]), int(lengths[i])
+        gbaes.ecb_ex(keys[int(reqs["key_index"][i])], x[a:a + n], alone[b:b + n], decrypt=bool(reqs["decrypt"][i]))
+    torch.cuda.synchronize()
+    assert torch.equal(alone, y)
+    xs = x.cpu().numpy()
+    ys = y.cpu().numpy()
+    for i in rng.choice(len(reqs), 40, replace=False):
+        a, b, n = int(in_off[i]), int(out_off[i]), int(lengths[i])
+        k = int(reqs["key_index"][i])
+        want = oracle.ecb(raw_keys[k], int(bits[k]), xs[a:a + n], decrypt=bool(reqs["decrypt"][i]))
+        assert np.array_equal(ys[b:b + n], want)
+    assert gbaes.device_status() == 0
+
+
+@pytest.mark.gpu
+def test_resident_sees_rewritten_inputs_and_in_place(gbaes):
+    """One resident kernel (long idle limit) serves requests on buffers that
+    change between them: an input rewritten from the host, and in-place
+    requests on a buffer it wrote itself.  Each result must reflect the data at
+    submission, not anything cached from earlier requests.  (While the kernel
+    runs it holds every SM, so the test moves data with copies only.)"""
+    rng = np.random.default_rng(21)
+    key = bytes(range(32))
+    k = gbaes.Key(key)
+    n = 1 << 16  # 1 MiB
+    x0 = rng.integers(0, 256, 16 * n, dtype=np.uint8)
+    x1 = rng.integers(0, 256, 16 * n, dtype=np.uint8)
+    x = torch.from_numpy(x0).cuda()
+    y = torch.zeros_like(x)
+    torch.cuda.synchronize()
+    srv = gbaes.Server([k], resident=True, resident_idle_us=2_000_000)
+
+    def run(i, src, dst, decrypt=False):
+        srv.submit(i, 0, src.data_ptr(), dst.data_ptr(), src.numel() // 16, decrypt)
+        srv.drain(10.0)
+        return dst.cpu().numpy()  # a device-to-host copy
+
+    first = run(0, x, y)
+    x.copy_(torch.from_numpy(x1))  # rewrite the input (host-to-device copy)
+    torch.cuda.current_stream().synchronize()  # (a device-wide sync would wait for the resident kernel)
+    second = run(1, x, y)
+    third = run(2, y, y)  # in place on the buffer the kernel just wrote
+    fourth = run(3, y, y, decrypt=True)
+    done = srv.poll_all()
+    launches = srv.stats()["batches"]
+    srv.close()
+    assert (done["status"] == 0).all() and len(done) == 4
+    assert launches == 1  # one kernel served all four
+    assert np.array_equal(first, oracle.ecb(key, 256, x0))
+    c = oracle.ecb(key, 256, x1)
+    assert np.array_equal(second, c)
+    assert np.array_equal(third, oracle.ecb(key, 256, c))
+    assert np.array_equal(fourth, c)
+
+
+@pytest.mark.gpu
+def test_resident_kernel_leaves_when_idle_and_is_relaunched(gbaes):
+    import time
+
+    rng = np.random.default_rng(5)
+    key = rng.integers(0, 256, 16, dtype=np.uint8).tobytes()
+    k = gbaes.Key(key)
+    x = torch.from_numpy(rng.integers(0, 256, 1 << 20, dtype=np.uint8)).cuda()
+    y = torch.zeros_like(x)
+    torch.cuda.synchronize()
+    srv = gbaes.Server([k], resident=True, resident_idle_us=300)
+    srv.submit(0, 0, x.data_ptr(), y.data_ptr(), 1 << 15)
+    srv.drain(10.0)
+    time.sleep(0.05)  # past the idle limit: the kernel has left
+    srv.submit(1, 0, x.data_ptr() + (1 << 19), y.data_ptr() + (1 << 19), 1 << 15)
+    srv.drain(10.0)
+    done = srv.poll_all()
+    launches = srv.stats()["batches"]
+    srv.close()
+    assert len(done) == 2 and (done["status"] == 0).all()
+    assert launches == 2
+    assert np.array_equal(y.cpu().numpy(), oracle.ecb(key, 128, x.cpu().numpy()))
+    assert gbaes.device_status() == 0
