@@ -11,8 +11,8 @@
 // of work: up to threads * BPT consecutive blocks of one request, thread i
 // taking blocks i, i + threads, ... so every load and store is coalesced.
 //
-// Thread 0 polls both directions' published-tile counters (its own direction
-// first), claims a tile with a compare-and-swap on the direction's device
+// Thread 0 polls both directions' published-tile counts, claims a tile (in
+// its own direction first) with a compare-and-swap on the direction's device
 // counter, and copies the tile record into shared memory.  A CTA switches its
 // tables to the other direction when only that direction has work, so every
 // live CTA serves every request.  Every thread fences its stores before the
@@ -41,12 +41,6 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
-}
-
-__device__ __forceinline__ uint64_t ld_acquire_sys(const uint64_t* p) {
-    uint64_t v;
-    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
 }
 
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
@@ -97,25 +91,34 @@ __device__ __forceinline__ uint4 lds_v4(uint32_t addr) {
 }
 
 // Thread 0: waits for a tile to claim.  Returns true with the tile's
-// direction and index, or false when the CTA should leave.
+// direction and index, or false when the CTA should leave.  One poll issues
+// the loads of both published counts, the stop word and both claim counters
+// together (one host-link round trip); after a successful claim, an acquire
+// fence orders the reads of the tile's record after the count that published
+// it.
 __device__ __forceinline__ bool claim_tile(const ResArgs& a, int dir, uint64_t t_start, int* tdir, uint64_t* tile) {
     const uint64_t idle_since = globaltimer_ns();
     for (;;) {
         const uint64_t now = globaltimer_ns();
-        if (ld_volatile_u32(&a.ctrl->stop) || now - t_start > a.lifetime_ns) return false;
+        uint64_t pub[2];
+        asm volatile("ld.relaxed.sys.global.v2.u64 {%0, %1}, [%2];" : "=l"(pub[0]), "=l"(pub[1]) : "l"(a.ctrl->pub) : "memory");
+        const uint32_t stop = ld_volatile_u32(&a.ctrl->stop);
+        unsigned long long c[2] = {ld_volatile_u64(&a.claim[0]), ld_volatile_u64(&a.claim[1])};
+        if (stop || now - t_start > a.lifetime_ns) return false;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int d = k ? dir ^ 1 : dir;
-            const uint64_t p = ld_acquire_sys(&a.ctrl->pub[d]);
-            unsigned long long c = ld_volatile_u64(&a.claim[d]);
-            while (c < p) {  // each failed swap returns a larger count: at most p - c tries
-                const unsigned long long old = atomicCAS(&a.claim[d], c, c + 1);
-                if (old == c) {
+            const uint64_t pd = d ? pub[1] : pub[0];  // (selects, not a runtime index into a local array)
+            unsigned long long cd = d ? c[1] : c[0];
+            while (cd < pd) {  // each failed swap returns a larger count: at most pub - c tries
+                const unsigned long long old = atomicCAS(&a.claim[d], cd, cd + 1);
+                if (old == cd) {
+                    asm volatile("fence.acq_rel.sys;" ::: "memory");
                     *tdir = d;
-                    *tile = c;
+                    *tile = cd;
                     return true;
                 }
-                c = old;
+                cd = old;
             }
         }
         if (now - idle_since > a.idle_ns) return false;
@@ -198,8 +201,10 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(const ResArgs a) {
             const uint64_t slot = (uint64_t)dir * a.ring_items + r2.z;
             const unsigned long long before = atomicAdd(&a.done[slot], (unsigned long long)n);
             if (before + n == item_blocks) {  // the request's last tile: every other tile was counted before
-                atomicExch(&a.done[slot], 0ull);
-                __threadfence_system();
+                // No other CTA touches the counter now; the reset is ordered
+                // before the status word, after which the slot may be reused.
+                asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(a.done + slot), "l"(0ull) : "memory");
+                __threadfence_system();  // acquire the other tiles' outputs, release them with ours
                 st_release_sys(&a.status[slot], seq);
             }
         }

@@ -462,6 +462,7 @@ static bool publish(aes_server* S, const Pending& p, uint64_t bytes) {
 
 static void scheduler_resident(aes_server* S) {
     if (!S->dryrun) cudaSetDevice(S->device);
+    double last_work = S->now();
     for (;;) {
         bool worked = take_inbox(S);
         // Completions: status words the kernel wrote.  Ring space is freed in
@@ -540,7 +541,15 @@ static void scheduler_resident(aes_server* S) {
                 fail_resident_inflight(S, rc);
             worked = true;
         }
-        if (!worked && !idle_wait(S, S->queue.empty() && !inflight)) break;
+        if (worked) {
+            last_work = S->now();
+        } else {
+            // Nothing to do: keep polling for 200 us after the last work (a
+            // condition-variable wake-up would add its latency to the next
+            // request), then sleep until a submission.
+            const bool idle = S->queue.empty() && !inflight;
+            if (!idle_wait(S, idle && S->now() - last_work > 200e-6)) break;
+        }
     }
     // Shutdown: everything has completed; ask the kernel to leave and wait for it.
     __atomic_store_n(&S->rctrl->stop, 1u, __ATOMIC_RELEASE);
