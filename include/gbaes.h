@@ -232,14 +232,16 @@ void aes_pipeline_free(aes_pipeline* pipe);
 
 /* Resident mode: instead of one batched-kernel launch per micro-batch, one
  * kernel stays on the GPU (one CTA per SM) and takes requests as they are
- * admitted.  The scheduler writes each request as tiles of threads *
- * blocks_per_thread blocks into a ring in mapped page-locked memory and
- * publishes them with a release store; a CTA claims a tile, enciphers it, and
- * the CTA that finishes a request's last tile writes its completion into a
- * status word in page-locked memory, which the scheduler polls.  No launch,
- * copy or event per request.  The kernel leaves after resident_idle_us
- * without work (or resident_lifetime_ms after its launch, or at shutdown) and
- * is relaunched when work arrives; while it runs it holds every SM, so other
+ * admitted.  The scheduler cuts each request into tiles of at most threads *
+ * blocks_per_thread blocks (spread over up to one tile per SM, at least 256
+ * blocks each), writes them into a ring in mapped page-locked memory and
+ * publishes them with a release store; CTAs take tiles with tickets from an
+ * atomic counter, and the CTA that finishes a request's last tile writes its
+ * completion into a status word in page-locked memory, which the scheduler
+ * polls.  No launch, copy or event per request.  The scheduler stops the
+ * kernel after resident_idle_us without work and before resident_lifetime_ms
+ * (its bound on the GPU) have passed, and relaunches it when work arrives;
+ * while it runs it holds every SM, so other
  * kernels on the device wait for it, and so does a device-wide synchronisation
  * (cudaDeviceSynchronize).  Request inputs must be complete in
  * device memory when submitted.  With AES_SERVER_DRYRUN, a host thread runs
@@ -253,13 +255,13 @@ typedef struct aes_server_config {
     uint64_t budget_bytes;      /* in+out bytes in flight (0 = 8 GiB) */
     int32_t nstreams;           /* stream slots, 1..64 (0 = 4) */
     int32_t flags;              /* AES_SERVER_* */
-    int32_t threads;            /* batched-kernel CTA size (0 = 512; resident mode: 1024) */
+    int32_t threads;            /* batched-kernel (or resident-kernel) CTA size (0 = 512) */
     int32_t blocks_per_thread;  /* 1, 2 or 4 (0 = 1) */
     uint32_t max_batch_msgs;    /* requests per batch (0 = 4096) */
     uint32_t dryrun_batch_us;   /* AES_SERVER_DRYRUN only: simulated time a batch spends "on the GPU" */
     uint64_t max_batch_blocks;  /* blocks per batch, also the largest request (0 = 2^22) */
-    uint32_t resident_idle_us;     /* AES_SERVER_RESIDENT: a CTA leaves after this long without work (0 = 2000) */
-    uint32_t resident_lifetime_ms; /* ... and at the latest this long after its launch (0 = 10000) */
+    uint32_t resident_idle_us;     /* AES_SERVER_RESIDENT: the kernel is stopped after this long without work (0 = 2000) */
+    uint32_t resident_lifetime_ms; /* ... and restarted before this long after its launch (0 = 10000) */
     uint32_t ring_tiles;           /* tile records per direction, a power of two (0 = 65536); must hold the
                                       largest request */
     uint32_t ring_items;           /* requests in flight per direction, a power of two (0 = 16384) */

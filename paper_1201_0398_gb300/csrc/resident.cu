@@ -11,20 +11,25 @@
 // of work: up to threads * BPT consecutive blocks of one request, thread i
 // taking blocks i, i + threads, ... so every load and store is coalesced.
 //
-// Thread 0 polls both directions' published-tile counts, claims a tile (in
-// its own direction first) with a compare-and-swap on the direction's device
-// counter, and copies the tile record into shared memory.  A CTA switches its
-// tables to the other direction when only that direction has work, so every
+// Thread 0 takes tickets (tile indices) from the directions' device counters
+// with atomic adds -- one always ready in its own direction, one in the other
+// direction when that has published tiles nobody has taken -- polls the
+// published-tile counts in page-locked memory, and copies a ticket's tile
+// record into shared memory once the tile is published.  (Claiming by
+// compare-and-swap instead serialised every claim behind one L2 atomic round
+// trip per success: with 152 CTAs polling, ~38 failed swaps per claim.)  A CTA
+// switches its tables to the other direction when its tile is there, so every
 // live CTA serves every request.  Every thread fences its stores before the
-// CTA's tile count goes into the request's done counter; the CTA that
-// completes a request resets the counter and writes the request's sequence
-// number to its status word with a system-scope release.
+// CTA's tile count goes into the request's done counter (an acquire-release
+// add); the CTA that completes a request resets the counter and writes the
+// request's sequence number to its status word with a system-scope release.
 //
-// Every wait is bounded: a CTA leaves once it has found nothing to claim for
-// idle_ns, once lifetime_ns have passed since its start, or when the host sets
-// the stop word (all three checked between tiles).  Claimed tiles are always
-// finished first, so the host relaunches the kernel whenever it has published
-// work and the kernel has ended.
+// Every wait is bounded: a CTA leaves when the host sets the stop word or once
+// lifetime_ns have passed since its start (both checked between tiles),
+// writing the tickets it still holds to the abandon list.  The host stops the
+// kernel (after it has stopped publishing) when it has been idle or is near
+// its lifetime, and before relaunching re-publishes any abandoned tile that was
+// published meanwhile and resets the ticket counters (resident.h).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -90,38 +95,77 @@ __device__ __forceinline__ uint4 lds_v4(uint32_t addr) {
     return v;
 }
 
-// Thread 0: waits for a tile to claim.  Returns true with the tile's
-// direction and index, or false when the CTA should leave.  One poll issues
-// the loads of both published counts, the stop word and both claim counters
-// together (one host-link round trip); after a successful claim, an acquire
-// fence orders the reads of the tile's record after the count that published
-// it.
-__device__ __forceinline__ bool claim_tile(const ResArgs& a, int dir, uint64_t t_start, int* tdir, uint64_t* tile) {
-    const uint64_t idle_since = globaltimer_ns();
+constexpr unsigned long long kNoTicket = ~0ull;
+
+// One direction's share of a poll: takes a ticket when the CTA holds none in
+// this direction and either it is the CTA's own direction (so a ticket is
+// ready for the next tile published there) or the direction has published
+// tiles nobody has taken; then says whether the held ticket's tile is published.
+__device__ __forceinline__ bool poll_dir(const ResArgs& a, int d, bool own, uint64_t pub, unsigned long long claim,
+                                         unsigned long long& held) {
+    if (held == kNoTicket && (own || claim < pub)) held = atomicAdd(&a.claim[d], 1ull);
+    return held != kNoTicket && held < pub;
+}
+
+__device__ __forceinline__ void abandon_ticket(const ResArgs& a, int d, unsigned long long held) {
+    if (held == kNoTicket) return;
+    const unsigned long long i = atomicAdd(&a.abandon_n[d], 1ull);
+    if (i < kAbandonCap)
+        a.abandon[(uint64_t)d * kAbandonCap + i] = held;
+    else
+        atomicOr(a.err, 8);
+}
+
+__device__ __forceinline__ void load_pub(const ResArgs& a, uint64_t& p0, uint64_t& p1) {
+    asm volatile("ld.relaxed.sys.global.v2.u64 {%0, %1}, [%2];" : "=l"(p0), "=l"(p1) : "l"(a.ctrl->pub) : "memory");
+}
+
+// Thread 0: the next tile to encipher (true), or false when the CTA should
+// leave.  h0/h1: the tickets the CTA holds (kNoTicket if none), kept across
+// calls.  One poll issues the loads of both published counts, the stop word
+// and both ticket counters together (one host-link round trip); before a
+// published tile's record is read, an acquire fence orders the read after the
+// count that published it.  The CTA leaves on the stop word or its lifetime,
+// unless a held ticket's tile has been published (it enciphers that first).
+__device__ __forceinline__ bool next_tile(const ResArgs& a, int dir, uint64_t t_start, unsigned long long& h0,
+                                          unsigned long long& h1, int* tdir, uint64_t* tile) {
     for (;;) {
         const uint64_t now = globaltimer_ns();
-        uint64_t pub[2];
-        asm volatile("ld.relaxed.sys.global.v2.u64 {%0, %1}, [%2];" : "=l"(pub[0]), "=l"(pub[1]) : "l"(a.ctrl->pub) : "memory");
+        uint64_t p0, p1;
+        load_pub(a, p0, p1);
         const uint32_t stop = ld_volatile_u32(&a.ctrl->stop);
-        unsigned long long c[2] = {ld_volatile_u64(&a.claim[0]), ld_volatile_u64(&a.claim[1])};
-        if (stop || now - t_start > a.lifetime_ns) return false;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int d = k ? dir ^ 1 : dir;
-            const uint64_t pd = d ? pub[1] : pub[0];  // (selects, not a runtime index into a local array)
-            unsigned long long cd = d ? c[1] : c[0];
-            while (cd < pd) {  // each failed swap returns a larger count: at most pub - c tries
-                const unsigned long long old = atomicCAS(&a.claim[d], cd, cd + 1);
-                if (old == cd) {
-                    asm volatile("fence.acq_rel.sys;" ::: "memory");
-                    *tdir = d;
-                    *tile = cd;
-                    return true;
-                }
-                cd = old;
-            }
+        const unsigned long long c0 = ld_volatile_u64(&a.claim[0]), c1 = ld_volatile_u64(&a.claim[1]);
+        int got = -1;
+        if (dir == 0) {
+            if (poll_dir(a, 0, true, p0, c0, h0))
+                got = 0;
+            else if (poll_dir(a, 1, false, p1, c1, h1))
+                got = 1;
+        } else {
+            if (poll_dir(a, 1, true, p1, c1, h1))
+                got = 1;
+            else if (poll_dir(a, 0, false, p0, c0, h0))
+                got = 0;
         }
-        if (now - idle_since > a.idle_ns) return false;
+        if (got >= 0) {
+            asm volatile("fence.acq_rel.sys;" ::: "memory");
+            *tdir = got;
+            if (got) {
+                *tile = h1;
+                h1 = kNoTicket;
+            } else {
+                *tile = h0;
+                h0 = kNoTicket;
+            }
+            return true;
+        }
+        if (stop || now - t_start > a.lifetime_ns) {
+            load_pub(a, p0, p1);  // fresh counts: a held tile published since the poll is enciphered first
+            if ((h0 != kNoTicket && h0 < p0) || (h1 != kNoTicket && h1 < p1)) continue;
+            abandon_ticket(a, 0, h0);
+            abandon_ticket(a, 1, h1);
+            return false;
+        }
         __nanosleep(200);
     }
 }
@@ -147,12 +191,13 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(const ResArgs a) {
     int dir = (int)(blockIdx.x & 1u);
     fill_tables(A, dir != 0);
     const uint64_t t_start = globaltimer_ns();
+    unsigned long long h0 = kNoTicket, h1 = kNoTicket;  // thread 0's tickets
     for (;;) {
         if (threadIdx.x == 0) {
             int tdir = dir;
             uint64_t tile = 0;
             uint32_t cmd = 1;
-            if (claim_tile(a, dir, t_start, &tdir, &tile)) {
+            if (next_tile(a, dir, t_start, h0, h1, &tdir, &tile)) {
                 const uint8_t* rec = (const uint8_t*)(a.tiles + (uint64_t)tdir * a.ring_tiles + (tile & (a.ring_tiles - 1)));
 #pragma unroll
                 for (int q = 0; q < 3; ++q) sts_v4(ctl + 16u * q, ld_volatile_v4(rec + 16 * q));
@@ -184,10 +229,14 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(const ResArgs a) {
         }
         if (threadIdx.x <= nr) sts_v4(kslot + 16u * threadIdx.x, __ldg(a.keys + (uint64_t)key_slot * 16u + threadIdx.x));
         __syncthreads();  // the tables (after a swap) and the key slot are in place
-        if (dir)
-            cipher_rt<true, BPT>(s, SmemKeys{kslot}, (int)nr, L0, L1);
-        else
-            cipher_rt<false, BPT>(s, SmemKeys{kslot}, (int)nr, L0, L1);
+        // Warps past the tile's last block skip the rounds: their lookups would
+        // take shared-memory cycles from the warps that have blocks.
+        if ((threadIdx.x & ~31u) < n) {
+            if (dir)
+                cipher_rt<true, BPT>(s, SmemKeys{kslot}, (int)nr, L0, L1);
+            else
+                cipher_rt<false, BPT>(s, SmemKeys{kslot}, (int)nr, L0, L1);
+        }
 #pragma unroll
         for (int b = 0; b < BPT; ++b) {
             const uint32_t i = threadIdx.x + (uint32_t)b * blockDim.x;
@@ -199,12 +248,19 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(const ResArgs a) {
             const uint64_t item_blocks = ((uint64_t)r1.y << 32) | r1.x;
             const uint64_t seq = ((uint64_t)r1.w << 32) | r1.z;
             const uint64_t slot = (uint64_t)dir * a.ring_items + r2.z;
-            const unsigned long long before = atomicAdd(&a.done[slot], (unsigned long long)n);
+            // Release: the CTA's outputs (fenced by every thread, then the
+            // barrier) before the count; acquire: the outputs of the tiles
+            // counted before it.
+            unsigned long long before;
+            asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
+                         : "=l"(before)
+                         : "l"(a.done + slot), "l"((unsigned long long)n)
+                         : "memory");
             if (before + n == item_blocks) {  // the request's last tile: every other tile was counted before
-                // No other CTA touches the counter now; the reset is ordered
-                // before the status word, after which the slot may be reused.
+                // No other CTA touches the counter now.  The release store
+                // orders the reset and every output it has acquired before the
+                // status word, after which the host may reuse the slot.
                 asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(a.done + slot), "l"(0ull) : "memory");
-                __threadfence_system();  // acquire the other tiles' outputs, release them with ours
                 st_release_sys(&a.status[slot], seq);
             }
         }

@@ -3,11 +3,15 @@
 //
 // The host writes each admitted request as tile records into page-locked
 // memory the GPU reads over the host link, then publishes them by advancing its
-// direction's tile counter (a release store).  CTAs of the resident kernel
-// claim published tiles one at a time from a device-memory counter, encipher
-// them, and count finished blocks per request; the CTA that finishes a
-// request's last block writes the request's sequence number into its status
-// word in page-locked memory, where the scheduler sees it.
+// direction's tile count (a release store).  CTAs of the resident kernel take
+// tickets (tile indices) from a device-memory counter with an atomic add, also
+// ahead of publication, and encipher a ticket's tile once it is published; they
+// count finished blocks per request, and the CTA that finishes a request's last
+// block writes the request's sequence number into its status word in
+// page-locked memory, where the scheduler sees it.  A CTA that leaves (stop
+// word or lifetime) writes the tickets it still holds to the abandon list; once
+// the kernel has ended, the host re-publishes the abandoned tiles that had been
+// published meanwhile and moves the counters back to the first tile nobody took.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -36,18 +40,21 @@ struct ResCtrl {
 };
 static_assert(sizeof(ResCtrl) == 64, "one cache line");
 
+constexpr uint32_t kAbandonCap = 1024;  // per direction (a CTA holds at most one ticket per direction)
+
 struct ResArgs {
-    const ResTile* tiles;       // [2][ring_tiles], device view of page-locked memory
-    const ResCtrl* ctrl;        // device view of page-locked memory
-    uint64_t* status;           // [2][ring_items], device view of page-locked memory
-    unsigned long long* claim;  // [2] device memory: next tile to claim per direction
-    unsigned long long* done;   // [2][ring_items] device memory: blocks finished per request slot
-    const uint4* keys;          // resident schedules, 256 bytes per slot
-    int* err;                   // the library's device status word
-    uint32_t ring_tiles;        // power of two
-    uint32_t ring_items;        // power of two
-    uint64_t idle_ns;           // a CTA leaves after this long without a tile to claim
-    uint64_t lifetime_ns;       // and, between tiles, once this long has passed since its start
+    const ResTile* tiles;           // [2][ring_tiles], device view of page-locked memory
+    const ResCtrl* ctrl;            // device view of page-locked memory
+    uint64_t* status;               // [2][ring_items], device view of page-locked memory
+    unsigned long long* claim;      // [2] device memory: next ticket (tile index) per direction
+    unsigned long long* done;       // [2][ring_items] device memory: blocks finished per request slot
+    unsigned long long* abandon;    // [2][kAbandonCap] device memory: tickets held by CTAs that left
+    unsigned long long* abandon_n;  // [2] device memory: tickets written to the abandon list
+    const uint4* keys;              // resident schedules, 256 bytes per slot
+    int* err;                       // the library's device status word
+    uint32_t ring_tiles;            // power of two
+    uint32_t ring_items;            // power of two
+    uint64_t lifetime_ns;           // a CTA leaves once this long has passed since its start
 };
 
 // Launches the resident kernel: one CTA per SM, `threads` threads each,

@@ -115,7 +115,8 @@ struct aes_server {
 
     // Resident mode (scheduler thread only, except where noted).
     bool resident = false;
-    uint32_t tile_blocks = 0;
+    uint32_t tile_blocks = 0;     // a tile's capacity: threads * blocks_per_thread
+    uint32_t spread = 1;          // CTAs of the resident kernel: requests are cut into up to this many tiles
     uint8_t* ring_mem = nullptr;  // page-locked and mapped (plain host memory in a dry run)
     ResCtrl* rctrl = nullptr;     // host views into ring_mem
     ResTile* rtiles = nullptr;
@@ -128,8 +129,11 @@ struct aes_server {
     uint64_t rrel_items[2] = {0, 0};  // requests up to this sequence number are finished
     std::deque<ResItem> rinflight[2];
     bool rlive = false;               // a kernel (or its dry-run stand-in) is running
-    // Dry run: one host thread runs the kernel's claim/record/count/status protocol.
-    std::vector<uint64_t> fake_claim, fake_done;  // stand-in thread only
+    bool rstopping = false;           // its stop word is set: nothing is published until it has ended
+    double rlaunch_s = 0;             // its launch
+    // Dry run: one host thread runs the kernel's ticket/record/count/status protocol.
+    std::vector<uint64_t> fake_claim, fake_done;  // stand-in thread, or the scheduler while none runs
+    std::vector<uint64_t> fake_abandon[2];
     std::thread fake;
     std::atomic<bool> fake_running{false};
 
@@ -334,53 +338,60 @@ static void scheduler_main(aes_server* S) {
 
 // ------------------------------------------------------------ resident mode
 
-// Dry-run stand-in for the resident kernel: one host thread claims published
-// tiles, "enciphers" each for dryrun_batch_us, counts blocks per request and
-// publishes completions, with the kernel's exits (stop word, idle, lifetime).
+// Dry-run stand-in for the resident kernel: one host thread follows the
+// kernel's ticket protocol (a ticket always held in its own direction, one in
+// the other when that has untaken published tiles), "enciphers" each tile for
+// dryrun_batch_us, counts blocks per request, publishes completions, and on
+// the stop word or its lifetime leaves, writing held tickets to the abandon list.
 static void fake_kernel_main(aes_server* S) {
     using clock = std::chrono::steady_clock;
     const clock::time_point start = clock::now();
-    clock::time_point idle_since = start;
     const uint32_t rt = S->rargs.ring_tiles, ri = S->rargs.ring_items;
+    constexpr uint64_t kNone = ~0ull;
+    uint64_t held[2] = {kNone, kNone};
     int dir = 0;
     for (;;) {
-        const clock::time_point now = clock::now();
-        if (__atomic_load_n(&S->rctrl->stop, __ATOMIC_ACQUIRE) ||
-            (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(now - start).count() > S->rargs.lifetime_ns)
-            break;
-        int tdir = -1;
-        uint64_t tile = 0;
-        for (int k = 0; k < 2 && tdir < 0; ++k) {
+        uint64_t pub[2] = {__atomic_load_n(&S->rctrl->pub[0], __ATOMIC_ACQUIRE),
+                           __atomic_load_n(&S->rctrl->pub[1], __ATOMIC_ACQUIRE)};
+        int got = -1;
+        for (int k = 0; k < 2 && got < 0; ++k) {
             const int d = k ? dir ^ 1 : dir;
-            const uint64_t pub = __atomic_load_n(&S->rctrl->pub[d], __ATOMIC_ACQUIRE);
-            if (S->fake_claim[d] < pub) {
-                tdir = d;
-                tile = S->fake_claim[d]++;
-            }
+            if (held[d] == kNone && (k == 0 || S->fake_claim[d] < pub[d])) held[d] = S->fake_claim[d]++;
+            if (held[d] != kNone && held[d] < pub[d]) got = d;
         }
-        if (tdir < 0) {
-            if ((uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(now - idle_since).count() >
-                S->rargs.idle_ns)
+        if (got < 0) {
+            const bool expired = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(clock::now() - start)
+                                     .count() > S->rargs.lifetime_ns;
+            if (__atomic_load_n(&S->rctrl->stop, __ATOMIC_ACQUIRE) || expired) {
+                bool published = false;
+                for (int d = 0; d < 2; ++d)
+                    published = published ||
+                                (held[d] != kNone && held[d] < __atomic_load_n(&S->rctrl->pub[d], __ATOMIC_ACQUIRE));
+                if (published) continue;
+                for (int d = 0; d < 2; ++d)
+                    if (held[d] != kNone) S->fake_abandon[d].push_back(held[d]);
                 break;
+            }
             std::this_thread::sleep_for(std::chrono::microseconds(20));
             continue;
         }
-        dir = tdir;
-        const ResTile R = S->rtiles[(uint64_t)tdir * rt + (tile & (rt - 1))];
+        dir = got;
+        const ResTile R = S->rtiles[(uint64_t)got * rt + (held[got] & (rt - 1))];
+        held[got] = kNone;
         if (S->cfg.dryrun_batch_us) std::this_thread::sleep_for(std::chrono::microseconds(S->cfg.dryrun_batch_us));
-        uint64_t& done = S->fake_done[(uint64_t)tdir * ri + R.item];
+        uint64_t& done = S->fake_done[(uint64_t)got * ri + R.item];
         done += R.nblocks;
         if (done == R.item_blocks) {
             done = 0;
-            __atomic_store_n(&S->rstatus[(uint64_t)tdir * ri + R.item], R.seq, __ATOMIC_RELEASE);
+            __atomic_store_n(&S->rstatus[(uint64_t)got * ri + R.item], R.seq, __ATOMIC_RELEASE);
         }
-        idle_since = clock::now();
     }
     S->fake_running.store(false, std::memory_order_release);
 }
 
 // Starts the kernel (or its dry-run stand-in).
 static int start_resident(aes_server* S) {
+    S->rlaunch_s = S->now();
     if (S->dryrun) {
         if (S->fake.joinable()) S->fake.join();  // the previous one has finished
         S->fake_running.store(true);
@@ -400,9 +411,59 @@ static bool resident_running(aes_server* S, int* err) {
     return false;
 }
 
+// After a kernel has ended: re-publishes every abandoned ticket whose tile had
+// been published (nobody enciphered it), moves each ticket counter back to the
+// first tile nobody took (tickets taken ahead of publication are void), and
+// clears the abandon list and the stop word for the next kernel.
+static int recover_resident(aes_server* S) {
+    const uint32_t rt = S->rargs.ring_tiles;
+    unsigned long long claim[2] = {0, 0}, n[2] = {0, 0};
+    std::vector<unsigned long long> ab(2 * (size_t)kAbandonCap, 0);
+    if (S->dryrun) {
+        if (S->fake.joinable()) S->fake.join();
+        for (int d = 0; d < 2; ++d) {
+            claim[d] = S->fake_claim[d];
+            n[d] = S->fake_abandon[d].size();
+            for (size_t i = 0; i < S->fake_abandon[d].size() && i < kAbandonCap; ++i)
+                ab[(size_t)d * kAbandonCap + i] = S->fake_abandon[d][i];
+        }
+    } else {
+        cudaError_t e = cudaMemcpy(claim, S->rargs.claim, sizeof claim, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(n, S->rargs.abandon_n, sizeof n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(ab.data(), S->rargs.abandon, ab.size() * sizeof(ab[0]), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(AES_ERR_CUDA, "resident recovery: %s", cudaGetErrorString(e));
+    }
+    for (int d = 0; d < 2; ++d) {
+        if (n[d] > kAbandonCap) return fail(AES_ERR_DEVICE, "resident kernel: abandon list overflowed");
+        const uint64_t pub = S->rpub[d];
+        claim[d] = std::min<unsigned long long>(claim[d], pub);
+        for (unsigned long long i = 0; i < n[d]; ++i) {
+            const uint64_t t = ab[(size_t)d * kAbandonCap + i];
+            if (t >= pub) continue;  // never published: void
+            if (S->rpub[d] + 1 - S->rrel_tiles[d] > rt) return fail(AES_ERR_STATE, "resident ring full during recovery");
+            S->rtiles[(uint64_t)d * rt + (S->rpub[d] & (rt - 1))] = S->rtiles[(uint64_t)d * rt + (t & (rt - 1))];
+            ++S->rpub[d];
+        }
+        __atomic_store_n(&S->rctrl->pub[d], S->rpub[d], __ATOMIC_RELEASE);
+    }
+    if (S->dryrun) {
+        for (int d = 0; d < 2; ++d) {
+            S->fake_claim[d] = claim[d];
+            S->fake_abandon[d].clear();
+        }
+    } else {
+        const unsigned long long zero[2] = {0, 0};
+        cudaError_t e = cudaMemcpy(S->rargs.claim, claim, sizeof claim, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(S->rargs.abandon_n, zero, sizeof zero, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(AES_ERR_CUDA, "resident recovery: %s", cudaGetErrorString(e));
+    }
+    __atomic_store_n(&S->rctrl->stop, 0u, __ATOMIC_RELEASE);
+    return AES_OK;
+}
+
 // Completes every published, unfinished request with `status` (the kernel has
 // failed or could not start: their work will not be done), frees their ring
-// space and moves the claim counters past their tiles, so that a later kernel
+// space and moves the ticket counters past their tiles, so that a later kernel
 // starts with the next request.  Called only while no kernel runs.
 static void fail_resident_inflight(aes_server* S, int status) {
     const double t = S->now();
@@ -413,22 +474,38 @@ static void fail_resident_inflight(aes_server* S, int status) {
             S->inflight_bytes -= it.bytes;
             complete(S, one, status, it.launch_s, t);
         }
-        if (!S->rinflight[d].empty()) {
-            const ResItem& last = S->rinflight[d].back();
-            S->rrel_tiles[d] = last.first_tile + last.ntiles;
-            S->rrel_items[d] = last.seq;
-            S->rinflight[d].clear();
-        }
+        S->rinflight[d].clear();
+        S->rrel_tiles[d] = S->rpub[d];
+        S->rrel_items[d] = S->ritems[d];
     }
     if (S->dryrun) {
-        for (int d = 0; d < 2; ++d) S->fake_claim[d] = S->rpub[d];
+        for (int d = 0; d < 2; ++d) {
+            S->fake_claim[d] = S->rpub[d];
+            S->fake_abandon[d].clear();
+        }
         std::fill(S->fake_done.begin(), S->fake_done.end(), 0);
     } else {
         unsigned long long claim[2] = {S->rpub[0], S->rpub[1]};
+        const unsigned long long zero[2] = {0, 0};
         cudaMemcpy(S->rargs.claim, claim, sizeof claim, cudaMemcpyHostToDevice);
+        cudaMemcpy(S->rargs.abandon_n, zero, sizeof zero, cudaMemcpyHostToDevice);
         cudaMemset(S->rargs.done, 0, sizeof(unsigned long long) * 2 * S->rargs.ring_items);
         cudaGetLastError();
     }
+    __atomic_store_n(&S->rctrl->stop, 0u, __ATOMIC_RELEASE);
+}
+
+constexpr uint64_t kMinSplitBlocks = 256;  // below this, splitting a request costs more than it saves
+
+// Blocks per tile for a request of n blocks: spread over up to one tile per
+// CTA (a tile's rounds are bound by its SM's shared-memory lookups, so
+// smaller tiles on more SMs finish sooner), but no smaller than
+// kMinSplitBlocks and no larger than a tile's capacity.  Tiles per request:
+// at most max(spread, ceil(n / capacity)).
+static uint64_t request_tile_blocks(const aes_server* S, uint64_t n) {
+    const uint64_t cap = S->tile_blocks;
+    const uint64_t lo = std::min<uint64_t>(kMinSplitBlocks, cap);
+    return std::min<uint64_t>(cap, std::max<uint64_t>(lo, (n + S->spread - 1) / S->spread));
 }
 
 // Writes request p as tile records and publishes them.  Returns false if the
@@ -436,7 +513,7 @@ static void fail_resident_inflight(aes_server* S, int status) {
 static bool publish(aes_server* S, const Pending& p, uint64_t bytes) {
     const int d = (int)p.r.decrypt;
     const uint32_t rt = S->rargs.ring_tiles, ri = S->rargs.ring_items;
-    const uint64_t tb = S->tile_blocks;
+    const uint64_t tb = request_tile_blocks(S, p.r.nblocks);
     const uint64_t ntiles = (p.r.nblocks + tb - 1) / tb;
     if (S->rpub[d] + ntiles - S->rrel_tiles[d] > rt || S->ritems[d] - S->rrel_items[d] >= ri) return false;
     const uint64_t seq = ++S->ritems[d];
@@ -463,6 +540,8 @@ static bool publish(aes_server* S, const Pending& p, uint64_t bytes) {
 static void scheduler_resident(aes_server* S) {
     if (!S->dryrun) cudaSetDevice(S->device);
     double last_work = S->now();
+    const double idle_s = 1e-6 * S->cfg.resident_idle_us;
+    const double restart_s = 0.8e-3 * S->cfg.resident_lifetime_ms;  // well before the kernel's own bound
     for (;;) {
         bool worked = take_inbox(S);
         // Completions: status words the kernel wrote.  Ring space is freed in
@@ -486,13 +565,27 @@ static void scheduler_resident(aes_server* S) {
                 S->rinflight[d].pop_front();
             }
         }
-        if (S->rlive) {
+        if (S->rlive) {  // has the kernel ended?
             int err = AES_OK;
-            S->rlive = resident_running(S, &err);
-            if (err != AES_OK) fail_resident_inflight(S, err);
+            if (!resident_running(S, &err)) {
+                S->rlive = false;
+                S->rstopping = false;
+                if (err == AES_OK) err = recover_resident(S);
+                if (err != AES_OK) fail_resident_inflight(S, err);
+                worked = true;
+            }
+        }
+        bool inflight = !S->rinflight[0].empty() || !S->rinflight[1].empty();
+        // Stop the kernel (no publishing until it has ended) when the server
+        // has been idle, or before the kernel reaches its lifetime bound.
+        const bool quiet = !inflight && S->queue.empty();
+        if (S->rlive && !S->rstopping &&
+            ((quiet && (S->now() - last_work > idle_s || S->stop.load())) || S->now() - S->rlaunch_s > restart_s)) {
+            __atomic_store_n(&S->rctrl->stop, 1u, __ATOMIC_RELEASE);
+            S->rstopping = true;
         }
         // Admission in arrival order while the budget and the ring have room.
-        while (!S->queue.empty()) {
+        while (!S->rstopping && !S->queue.empty()) {
             const Pending& p = S->queue.front();
             const uint64_t b = request_bytes(p.r);
             if (p.r.nblocks == 0) {
@@ -528,7 +621,7 @@ static void scheduler_resident(aes_server* S) {
             std::lock_guard<std::mutex> lk(S->stats_mu);
             S->stats.max_queue = std::max<uint64_t>(S->stats.max_queue, S->queue.size());
         }
-        const bool inflight = !S->rinflight[0].empty() || !S->rinflight[1].empty();
+        inflight = !S->rinflight[0].empty() || !S->rinflight[1].empty();
         if (inflight && !S->rlive) {  // published work and no kernel: (re)launch
             const int rc = start_resident(S);
             {
@@ -546,18 +639,13 @@ static void scheduler_resident(aes_server* S) {
         } else {
             // Nothing to do: keep polling for 200 us after the last work (a
             // condition-variable wake-up would add its latency to the next
-            // request), then sleep until a submission.
-            const bool idle = S->queue.empty() && !inflight;
+            // request), then sleep until a submission.  Not while a kernel is
+            // running or stopping: its end must be seen.
+            const bool idle = S->queue.empty() && !inflight && !S->rlive;
             if (!idle_wait(S, idle && S->now() - last_work > 200e-6)) break;
         }
     }
-    // Shutdown: everything has completed; ask the kernel to leave and wait for it.
-    __atomic_store_n(&S->rctrl->stop, 1u, __ATOMIC_RELEASE);
-    if (S->dryrun) {
-        if (S->fake.joinable()) S->fake.join();
-    } else if (S->rstream) {
-        cudaStreamSynchronize(S->rstream);
-    }
+    // Shutdown: everything has completed and the kernel has been stopped.
 }
 
 static int enqueue(aes_server* S, const aes_server_request& r, double arrival) {
@@ -622,6 +710,11 @@ static void producer_main(aes_server* S) {
 }
 
 static void destroy_server(aes_server* S) {
+    if (S->rctrl) {  // the scheduler has seen the kernel end; a safeguard before anything it reads is freed
+        __atomic_store_n(&S->rctrl->stop, 1u, __ATOMIC_RELEASE);
+        if (S->fake.joinable()) S->fake.join();
+        if (S->rstream) cudaStreamSynchronize(S->rstream);
+    }
     for (Slot& slot : S->slots) {
         if (slot.done) cudaEventDestroy(slot.done);
         if (slot.stream) cudaStreamDestroy(slot.stream);
@@ -635,6 +728,8 @@ static void destroy_server(aes_server* S) {
         if (S->ring_mem) cudaFreeHost(S->ring_mem);
         if (S->rargs.claim) cudaFree(S->rargs.claim);
         if (S->rargs.done) cudaFree(S->rargs.done);
+        if (S->rargs.abandon) cudaFree(S->rargs.abandon);
+        if (S->rargs.abandon_n) cudaFree(S->rargs.abandon_n);
         if (S->rstream) cudaStreamDestroy(S->rstream);
     }
     delete S;
@@ -662,6 +757,9 @@ static int setup_resident(aes_server* S) {
         if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&dev_view, S->ring_mem, 0);
         if (e == cudaSuccess) e = cudaMalloc(&S->rargs.claim, 2 * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMalloc(&S->rargs.done, 2 * (size_t)ri * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&S->rargs.abandon, 2 * (size_t)kAbandonCap * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&S->rargs.abandon_n, 2 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemset(S->rargs.abandon_n, 0, 2 * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMemset(S->rargs.claim, 0, 2 * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMemset(S->rargs.done, 0, 2 * (size_t)ri * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->rstream, cudaStreamNonBlocking);
@@ -682,7 +780,15 @@ static int setup_resident(aes_server* S) {
     S->rargs.err = S->status;
     S->rargs.ring_tiles = rt;
     S->rargs.ring_items = ri;
-    S->rargs.idle_ns = 1000ull * c.resident_idle_us;
+    if (!S->dryrun) {
+        DeviceInfo info;
+        int rc = current_device_info(&info);
+        if (rc) return rc;
+        S->spread = (uint32_t)info.sms;
+    } else {
+        S->spread = 8;
+    }
+    S->spread = std::min(S->spread, rt);  // a request never needs more ring than ring_tiles
     S->rargs.lifetime_ns = 1000000ull * c.resident_lifetime_ms;
     return AES_OK;
 }
@@ -697,7 +803,7 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
     if (config) cfg = *config;
     if (cfg.budget_bytes == 0) cfg.budget_bytes = (uint64_t)8 << 30;
     if (cfg.nstreams == 0) cfg.nstreams = 4;
-    if (cfg.threads == 0) cfg.threads = (cfg.flags & AES_SERVER_RESIDENT) ? 1024 : 512;
+    if (cfg.threads == 0) cfg.threads = 512;
     if (cfg.blocks_per_thread == 0) cfg.blocks_per_thread = 1;
     if (cfg.max_batch_msgs == 0) cfg.max_batch_msgs = 4096;
     if (cfg.max_batch_blocks == 0) cfg.max_batch_blocks = (uint64_t)1 << 22;
