@@ -427,10 +427,13 @@ static int recover_resident(aes_server* S) {
             for (size_t i = 0; i < S->fake_abandon[d].size() && i < kAbandonCap; ++i)
                 ab[(size_t)d * kAbandonCap + i] = S->fake_abandon[d][i];
         }
-    } else {
-        cudaError_t e = cudaMemcpy(claim, S->rargs.claim, sizeof claim, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) e = cudaMemcpy(n, S->rargs.abandon_n, sizeof n, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) e = cudaMemcpy(ab.data(), S->rargs.abandon, ab.size() * sizeof(ab[0]), cudaMemcpyDeviceToHost);
+    } else {  // on the kernel's own stream: other streams' work does not delay the recovery
+        cudaStream_t st = S->rstream;
+        cudaError_t e = cudaMemcpyAsync(claim, S->rargs.claim, sizeof claim, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(n, S->rargs.abandon_n, sizeof n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ab.data(), S->rargs.abandon, ab.size() * sizeof(ab[0]), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return fail(AES_ERR_CUDA, "resident recovery: %s", cudaGetErrorString(e));
     }
     for (int d = 0; d < 2; ++d) {
@@ -453,8 +456,10 @@ static int recover_resident(aes_server* S) {
         }
     } else {
         const unsigned long long zero[2] = {0, 0};
-        cudaError_t e = cudaMemcpy(S->rargs.claim, claim, sizeof claim, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(S->rargs.abandon_n, zero, sizeof zero, cudaMemcpyHostToDevice);
+        cudaStream_t st = S->rstream;
+        cudaError_t e = cudaMemcpyAsync(S->rargs.claim, claim, sizeof claim, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(S->rargs.abandon_n, zero, sizeof zero, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // (the sources live on this stack)
         if (e != cudaSuccess) return fail(AES_ERR_CUDA, "resident recovery: %s", cudaGetErrorString(e));
     }
     __atomic_store_n(&S->rctrl->stop, 0u, __ATOMIC_RELEASE);
@@ -487,9 +492,11 @@ static void fail_resident_inflight(aes_server* S, int status) {
     } else {
         unsigned long long claim[2] = {S->rpub[0], S->rpub[1]};
         const unsigned long long zero[2] = {0, 0};
-        cudaMemcpy(S->rargs.claim, claim, sizeof claim, cudaMemcpyHostToDevice);
-        cudaMemcpy(S->rargs.abandon_n, zero, sizeof zero, cudaMemcpyHostToDevice);
-        cudaMemset(S->rargs.done, 0, sizeof(unsigned long long) * 2 * S->rargs.ring_items);
+        cudaStream_t st = S->rstream;
+        cudaMemcpyAsync(S->rargs.claim, claim, sizeof claim, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(S->rargs.abandon_n, zero, sizeof zero, cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(S->rargs.done, 0, sizeof(unsigned long long) * 2 * S->rargs.ring_items, st);
+        cudaStreamSynchronize(st);
         cudaGetLastError();
     }
     __atomic_store_n(&S->rctrl->stop, 0u, __ATOMIC_RELEASE);
