@@ -21,6 +21,8 @@ six launches, 6 GiB of plaintext-equivalent bytes per step and GPU.  The buffers
   batched   10,000 messages (log-uniform 16 B - 4 MiB, own key each, key sizes
             2:1:1, mixed directions) in one persistent launch, against the same
             messages issued as 10,000 single-message launches.
+  modes     CTR and CBC decryption (Section 3) on the 1 GiB AES-128/256 buffers:
+            GB/s and fraction of the lookup roofline.
   serving   open-loop Poisson arrivals (200k req/s for 10 s, 64 B - 1 MiB, 1,024
             resident keys, 8 GiB budget) through the server in resident mode (one
             kernel stays on the GPU and takes requests from a ring in page-locked
@@ -72,6 +74,7 @@ def parse_args():
     p.add_argument("--no-batched", action="store_true", help="skip the batched (10,000-message) section")
     p.add_argument("--batch-steps", type=int, default=10)
     p.add_argument("--no-serving", action="store_true", help="skip the serving (open-loop) section")
+    p.add_argument("--no-modes", action="store_true", help="skip the CTR / CBC-decryption section")
     p.add_argument("--serve-seconds", type=float, default=10.0)
     p.add_argument("--sweep", action="store_true",
                    help="size sweep 4 KiB - 16 GiB (powers of 4), AES-128/256 encrypt, table vs bitsliced kernel")
@@ -433,6 +436,11 @@ def run_ours(args):
         e2e = run_e2e(g, torch, x, keys, kernel, stream, size, bytes_per_step,
                       args.e2e_steps or max(3, args.steps // 20), ranks, dev)
 
+    # ---- the other parallel modes of Section 3 on the same 1 GiB buffers
+    modes = None
+    if not args.no_modes and kernel == g.KERNEL_TABLE:
+        modes = bench_modes(g, torch, x, c, p, keys, stream, size, sms, f_max)
+
     batched = None
     if not args.no_batched:
         for t in (x, c, p):
@@ -473,9 +481,36 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(ops) * args.steps,
             "clocks": clk, "ops": op_stats, "tuned_shapes": {k: f"{v['threads']}x{v['blocks_per_thread']}"
                                                              for k, v in tuned.items()},
-            "batched": batched, "serving": serving,
+            "batched": batched, "serving": serving, "modes": modes,
         }), flush=True)
     dist.teardown(ranks)
+
+
+def bench_modes(g, torch, x, c, p, keys, stream, size, sms, f_max, reps=10):
+    """CTR (big-endian 128-bit counter) and CBC decryption (Eq. 2) on the 1 GiB
+    AES-128 and AES-256 buffers, one launch each, CUDA events on the launching
+    stream: GB/s of plaintext and the fraction of the same shared-memory lookup
+    roofline as ECB (the modes add one 16-byte XOR per block, and CBC one
+    cache-resident neighbour load)."""
+    iv = bytes(range(16))
+    out = {}
+    for bits in (128, 256):
+        for name, fn in (("ctr", lambda: g.ctr_xcrypt(keys[bits], iv, x[bits], c[bits], stream=stream)),
+                         ("cbc_dec", lambda: g.cbc_decrypt(keys[bits], iv, x[bits], p[bits], stream=stream))):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = size / (ms / 1e3) / 1e9
+            r = sms * LOOKUPS_PER_CLK_PER_SM * f_max / NR[bits] / 1e9
+            out[f"{name}_{bits}"] = {"ms": ms, "gbs": gbs, "smem_roofline_gbs": r, "frac": gbs / r}
+    return out
 
 
 def bench_batched(g, args, stream, ranks):

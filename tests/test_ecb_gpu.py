@@ -202,6 +202,42 @@ def test_one_gib_single_launch(gbaes, bits):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("bits", (128, 256))
+@pytest.mark.parametrize("kind", (oracle.CTR_BE128, oracle.CTR_LE32_CARRY))
+def test_ctr_and_cbc_one_gib(gbaes, bits, kind):
+    """The modes at the bench's size (1 GiB, 2^26 blocks, one launch each): the
+    CTR keystream (output XOR input) on 2^14 sampled blocks equals the oracle's
+    encryption of those blocks' counter blocks, and CTR applied twice gives the
+    input back everywhere; CBC decryption on sampled blocks (the first, whose
+    predecessor is the IV, and the last included) equals the oracle's
+    decryption of the block XOR the previous ciphertext block."""
+    key = workloads.random_key(90 + bits, bits)
+    k = gbaes.Key(key)
+    x = workloads.device_bytes(91 + bits, workloads.GiB)
+    n = x.numel() // 16
+    iv = bytes(range(0xF0, 0x100))  # low bytes near a carry
+    rng = np.random.default_rng(bits + kind)
+    idx = np.concatenate([[0, 1, n - 1], rng.choice(n, 1 << 14, replace=False)])
+    ti = torch.from_numpy(idx).cuda()
+    xb = host(x.view(-1, 16)[ti])
+    c = gbaes.ctr_xcrypt(k, iv, x, kind=kind)
+    ks = host(c.view(-1, 16)[ti]) ^ xb
+    ctrs = np.frombuffer(b"".join(oracle.counter_block(iv, int(i), kind) for i in idx), np.uint8)
+    assert np.array_equal(ks.reshape(-1), oracle.ecb(key, bits, ctrs))
+    assert torch.equal(gbaes.ctr_xcrypt(k, iv, c, kind=kind), x)
+    del c
+    if kind == oracle.CTR_BE128:
+        d = gbaes.cbc_decrypt(k, iv, x)
+        prev_idx = torch.from_numpy(np.maximum(idx - 1, 0)).cuda()
+        prev = host(x.view(-1, 16)[prev_idx])
+        prev[idx == 0] = np.frombuffer(iv, np.uint8)
+        want = oracle.ecb(key, bits, xb.reshape(-1), decrypt=True).reshape(-1, 16) ^ prev
+        assert np.array_equal(host(d.view(-1, 16)[ti]), want)
+        del d
+    del x
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("gib", (4, 16))
 def test_sweep_top_sizes_sampled(gbaes, gib):
     """The largest sweep points (4 and 16 GiB; 2^28 and 2^30 blocks): 64-bit
