@@ -79,6 +79,9 @@ def parse_args():
     p.add_argument("--sweep", action="store_true",
                    help="size sweep 4 KiB - 16 GiB (powers of 4), AES-128/256 encrypt, table vs bitsliced kernel")
     p.add_argument("--sweep-max-gib", type=int, default=16)
+    p.add_argument("--serve-sweep", action="store_true",
+                   help="serving latency against offered load (both server modes), one JSON line per point")
+    p.add_argument("--serve-sweep-seconds", type=float, default=2.0)
     return p.parse_args()
 
 
@@ -715,8 +718,32 @@ def run_cpu_sweep():
                               "matches_oracle": bool(ok)}), flush=True)
 
 
+def run_serve_sweep(args):
+    """Open-loop serving at 200k, 400k, 800k and 1.6M requests/s (the serving
+    workload's sizes and keys), through the resident kernel and through launch
+    per micro-batch: one JSON line per (mode, rate) with GB/s and latency
+    percentiles."""
+    import torch
+
+    from paper_1201_0398_gb300 import load, serving
+
+    load()
+    for rate in (200_000.0, 400_000.0, 800_000.0, 1_600_000.0):
+        for resident in (True, False):
+            r = serving.run(rate=rate, duration_s=args.serve_sweep_seconds, check_last=200, resident=resident)
+            torch.cuda.empty_cache()
+            keep = ("mode", "value", "offered_gbs", "requests", "completed_ok", "p50_ms", "p99_ms", "p999_ms",
+                    "max_ms", "p50_queue_ms", "p50_service_ms", "max_queue", "max_inflight_bytes", "shape",
+                    "mismatches", "mean_batch_msgs")
+            print(json.dumps({"sweep": "serving", "rate": rate, "seconds": args.serve_sweep_seconds,
+                              **{k: r[k] for k in keep if k in r}}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.serve_sweep:
+        run_serve_sweep(args)
+        return
     if args.sweep:
         run_sweep(args)
         run_cpu_sweep()

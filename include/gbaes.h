@@ -256,7 +256,7 @@ typedef struct aes_server_config {
     int32_t nstreams;           /* stream slots, 1..64 (0 = 4) */
     int32_t flags;              /* AES_SERVER_* */
     int32_t threads;            /* batched-kernel (or resident-kernel) CTA size (0 = 512) */
-    int32_t blocks_per_thread;  /* 1, 2 or 4 (0 = 1) */
+    int32_t blocks_per_thread;  /* 1, 2 or 4 (0 = 1; resident mode: 2) */
     uint32_t max_batch_msgs;    /* requests per batch (0 = 4096) */
     uint32_t dryrun_batch_us;   /* AES_SERVER_DRYRUN only: simulated time a batch spends "on the GPU" */
     uint64_t max_batch_blocks;  /* blocks per batch, also the largest request (0 = 2^22) */

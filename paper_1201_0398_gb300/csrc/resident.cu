@@ -21,8 +21,9 @@
 // switches its tables to the other direction when its tile is there, so every
 // live CTA serves every request.  Every thread fences its stores before the
 // CTA's tile count goes into the request's done counter (an acquire-release
-// add); the CTA that completes a request resets the counter and writes the
-// request's sequence number to its status word with a system-scope release.
+// add); the CTA that completes a request resets the counter and appends the
+// request to the completion queue, the entry's tag last with a system-scope
+// release.
 //
 // Every wait is bounded: a CTA leaves when the host sets the stop word or once
 // lifetime_ns have passed since its start (both checked between tiles),
@@ -257,11 +258,17 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(const ResArgs a) {
                          : "l"(a.done + slot), "l"((unsigned long long)n)
                          : "memory");
             if (before + n == item_blocks) {  // the request's last tile: every other tile was counted before
-                // No other CTA touches the counter now.  The release store
-                // orders the reset and every output it has acquired before the
-                // status word, after which the host may reuse the slot.
+                // No other CTA touches the counter now.  The entry's tag is
+                // written last with a release store: it orders the reset, the
+                // entry and every output this thread has acquired before it;
+                // after it the host may reuse the request's slot.
                 asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(a.done + slot), "l"(0ull) : "memory");
-                st_release_sys(&a.status[slot], seq);
+                const unsigned long long i = atomicAdd(a.cq_next, 1ull);
+                ResDone* e = a.cq + (i & (a.cq_size - 1));
+                asm volatile("st.relaxed.sys.global.u64 [%0], %1;" ::"l"(&e->what),
+                             "l"(((uint64_t)dir << 63) | seq)
+                             : "memory");
+                st_release_sys(&e->tag, i + 1);
             }
         }
     }

@@ -7,8 +7,8 @@
 // tickets (tile indices) from a device-memory counter with an atomic add, also
 // ahead of publication, and encipher a ticket's tile once it is published; they
 // count finished blocks per request, and the CTA that finishes a request's last
-// block writes the request's sequence number into its status word in
-// page-locked memory, where the scheduler sees it.  A CTA that leaves (stop
+// block appends (direction, request number) to a completion queue in
+// page-locked memory, which the scheduler reads in order.  A CTA that leaves (stop
 // word or lifetime) writes the tickets it still holds to the abandon list; once
 // the kernel has ended, the host re-publishes the abandoned tiles that had been
 // published meanwhile and moves the counters back to the first tile nobody took.
@@ -28,7 +28,7 @@ struct ResTile {
     uint64_t seq;          // request number in its direction, from 1
     uint32_t nblocks;      // blocks in this tile (>= 1)
     uint32_t key_slot;     // schedule slot in the resident key table (2 * key index + direction)
-    uint32_t item;         // request slot: index of its done counter and status word
+    uint32_t item;         // request slot: index of its done counter
     uint32_t nr;           // rounds: 10, 12 or 14
 };
 static_assert(sizeof(ResTile) == 48, "tile records are three 16-byte words");
@@ -42,10 +42,18 @@ static_assert(sizeof(ResCtrl) == 64, "one cache line");
 
 constexpr uint32_t kAbandonCap = 1024;  // per direction (a CTA holds at most one ticket per direction)
 
+// One completion: entry i of the completion queue holds tag = i + 1 (written
+// last, with a release store) and what = direction << 63 | request number.
+struct ResDone {
+    uint64_t tag;
+    uint64_t what;
+};
+
 struct ResArgs {
     const ResTile* tiles;           // [2][ring_tiles], device view of page-locked memory
     const ResCtrl* ctrl;            // device view of page-locked memory
-    uint64_t* status;               // [2][ring_items], device view of page-locked memory
+    ResDone* cq;                    // [cq_size] completion queue, device view of page-locked memory
+    unsigned long long* cq_next;    // device memory: completions written so far
     unsigned long long* claim;      // [2] device memory: next ticket (tile index) per direction
     unsigned long long* done;       // [2][ring_items] device memory: blocks finished per request slot
     unsigned long long* abandon;    // [2][kAbandonCap] device memory: tickets held by CTAs that left
@@ -54,6 +62,7 @@ struct ResArgs {
     int* err;                       // the library's device status word
     uint32_t ring_tiles;            // power of two
     uint32_t ring_items;            // power of two
+    uint32_t cq_size;               // power of two, 2 * ring_items (requests in flight, both directions)
     uint64_t lifetime_ns;           // a CTA leaves once this long has passed since its start
 };
 

@@ -91,7 +91,9 @@ struct aes_server {
     std::mutex in_mu;
     std::condition_variable in_cv;  // wakes an idle scheduler
     std::vector<Pending> inbox;
+    std::atomic<size_t> inbox_n{0};  // inbox.size(), readable without the lock
     std::vector<uint64_t> cancels;  // ids to cancel if still waiting for admission
+    std::atomic<size_t> cancels_n{0};
     std::deque<Pending> queue;  // scheduler thread only
     uint64_t inflight_bytes = 0;  // scheduler thread only
     uint64_t batch_counter = 0;   // scheduler thread only
@@ -116,11 +118,13 @@ struct aes_server {
     // Resident mode (scheduler thread only, except where noted).
     bool resident = false;
     uint32_t tile_blocks = 0;     // a tile's capacity: threads * blocks_per_thread
-    uint32_t spread = 1;          // CTAs of the resident kernel: requests are cut into up to this many tiles
+    uint32_t spread = 1;          // CTAs of the resident kernel
+    uint64_t rtiles_open = 0;     // tiles of published, unfinished requests
     uint8_t* ring_mem = nullptr;  // page-locked and mapped (plain host memory in a dry run)
     ResCtrl* rctrl = nullptr;     // host views into ring_mem
     ResTile* rtiles = nullptr;
-    uint64_t* rstatus = nullptr;
+    ResDone* rcq = nullptr;       // completion queue (host view)
+    uint64_t rcq_head = 0;        // completions consumed
     ResArgs rargs{};              // device views
     cudaStream_t rstream = nullptr;
     uint64_t rpub[2] = {0, 0};        // tiles published per direction
@@ -133,6 +137,7 @@ struct aes_server {
     double rlaunch_s = 0;             // its launch
     // Dry run: one host thread runs the kernel's ticket/record/count/status protocol.
     std::vector<uint64_t> fake_claim, fake_done;  // stand-in thread, or the scheduler while none runs
+    uint64_t fake_cq_next = 0;
     std::vector<uint64_t> fake_abandon[2];
     std::thread fake;
     std::atomic<bool> fake_running{false};
@@ -225,14 +230,18 @@ static int launch_slot(aes_server* S, Slot& slot) {
 static bool take_inbox(aes_server* S) {
     bool worked = false;
     std::vector<uint64_t> cancels;
+    if (S->inbox_n.load(std::memory_order_acquire) == 0 && !S->cancels_n.load(std::memory_order_acquire))
+        return false;  // nothing new: leave the lock to the producers
     {
         std::lock_guard<std::mutex> lk(S->in_mu);
         if (!S->inbox.empty()) {
             for (Pending& p : S->inbox) S->queue.push_back(p);
             S->inbox.clear();
+            S->inbox_n.store(0, std::memory_order_release);
             worked = true;
         }
         cancels.swap(S->cancels);
+        S->cancels_n.store(0, std::memory_order_release);
     }
     if (!cancels.empty()) {  // only requests not yet admitted can be cancelled
         std::vector<Pending> gone;
@@ -383,7 +392,10 @@ static void fake_kernel_main(aes_server* S) {
         done += R.nblocks;
         if (done == R.item_blocks) {
             done = 0;
-            __atomic_store_n(&S->rstatus[(uint64_t)got * ri + R.item], R.seq, __ATOMIC_RELEASE);
+            const uint64_t i = S->fake_cq_next++;
+            ResDone* e = &S->rcq[i & (S->rargs.cq_size - 1)];
+            __atomic_store_n(&e->what, ((uint64_t)got << 63) | R.seq, __ATOMIC_RELAXED);
+            __atomic_store_n(&e->tag, i + 1, __ATOMIC_RELEASE);
         }
     }
     S->fake_running.store(false, std::memory_order_release);
@@ -483,6 +495,7 @@ static void fail_resident_inflight(aes_server* S, int status) {
         S->rrel_tiles[d] = S->rpub[d];
         S->rrel_items[d] = S->ritems[d];
     }
+    S->rtiles_open = 0;
     if (S->dryrun) {
         for (int d = 0; d < 2; ++d) {
             S->fake_claim[d] = S->rpub[d];
@@ -504,15 +517,18 @@ static void fail_resident_inflight(aes_server* S, int status) {
 
 constexpr uint64_t kMinSplitBlocks = 256;  // below this, splitting a request costs more than it saves
 
-// Blocks per tile for a request of n blocks: spread over up to one tile per
-// CTA (a tile's rounds are bound by its SM's shared-memory lookups, so
-// smaller tiles on more SMs finish sooner), but no smaller than
-// kMinSplitBlocks and no larger than a tile's capacity.  Tiles per request:
-// at most max(spread, ceil(n / capacity)).
+// Blocks per tile for a request of n blocks: spread over the CTAs that have
+// nothing to do (the CTA count minus the tiles of unfinished requests; a
+// tile's rounds are bound by its SM's shared-memory lookups, so smaller tiles
+// on idle SMs finish sooner), but no smaller than kMinSplitBlocks and no
+// larger than a tile's capacity.  Under load the CTAs are busy and requests go
+// out in whole tiles (splitting then only adds per-tile overhead).  Tiles per
+// request: at most max(spread, ceil(n / capacity)).
 static uint64_t request_tile_blocks(const aes_server* S, uint64_t n) {
     const uint64_t cap = S->tile_blocks;
     const uint64_t lo = std::min<uint64_t>(kMinSplitBlocks, cap);
-    return std::min<uint64_t>(cap, std::max<uint64_t>(lo, (n + S->spread - 1) / S->spread));
+    const uint64_t idle = S->rtiles_open < S->spread ? S->spread - S->rtiles_open : 1;
+    return std::min<uint64_t>(cap, std::max<uint64_t>(lo, (n + idle - 1) / idle));
 }
 
 // Writes request p as tile records and publishes them.  Returns false if the
@@ -539,6 +555,7 @@ static bool publish(aes_server* S, const Pending& p, uint64_t bytes) {
     }
     ResItem it{p, seq, slot, S->rpub[d], ntiles, bytes, S->now(), false};
     S->rpub[d] += ntiles;
+    S->rtiles_open += ntiles;
     __atomic_store_n(&S->rctrl->pub[d], S->rpub[d], __ATOMIC_RELEASE);  // records before the count
     S->rinflight[d].push_back(it);
     return true;
@@ -547,30 +564,51 @@ static bool publish(aes_server* S, const Pending& p, uint64_t bytes) {
 static void scheduler_resident(aes_server* S) {
     if (!S->dryrun) cudaSetDevice(S->device);
     double last_work = S->now();
+    std::vector<aes_server_completion> finished;
     const double idle_s = 1e-6 * S->cfg.resident_idle_us;
     const double restart_s = 0.8e-3 * S->cfg.resident_lifetime_ms;  // well before the kernel's own bound
     for (;;) {
         bool worked = take_inbox(S);
-        // Completions: status words the kernel wrote.  Ring space is freed in
-        // publication order (a request's tiles and slot are reused only once it
-        // and every request before it in its direction have finished).
+        // Completions: new entries of the completion queue, in order.  Ring
+        // space is freed in publication order (a request's tiles and slot are
+        // reused only once it and every request before it in its direction
+        // have finished).
+        finished.clear();
+        for (;;) {
+            const ResDone* e = &S->rcq[S->rcq_head & (S->rargs.cq_size - 1)];
+            if (__atomic_load_n(&e->tag, __ATOMIC_ACQUIRE) != S->rcq_head + 1) break;
+            const uint64_t what = __atomic_load_n(&e->what, __ATOMIC_RELAXED);
+            ++S->rcq_head;
+            const int d = (int)(what >> 63);
+            const uint64_t seq = what & ~(1ull << 63);
+            std::deque<ResItem>& q = S->rinflight[d];
+            if (q.empty() || seq < q.front().seq || seq - q.front().seq >= q.size()) continue;  // (not in flight)
+            ResItem& it = q[seq - q.front().seq];
+            if (it.done) continue;
+            it.done = true;
+            S->inflight_bytes -= it.bytes;
+            S->rtiles_open -= it.ntiles;
+            finished.push_back(aes_server_completion{it.p.r.id, AES_OK, 1, it.p.arrival, it.launch_s, S->now()});
+        }
         for (int d = 0; d < 2; ++d) {
-            for (ResItem& it : S->rinflight[d]) {
-                if (it.done) continue;
-                const uint64_t* w = &S->rstatus[(uint64_t)d * S->rargs.ring_items + it.slot];
-                if (__atomic_load_n(w, __ATOMIC_ACQUIRE) != it.seq) continue;
-                it.done = true;
-                S->inflight_bytes -= it.bytes;
-                std::vector<Pending> one{it.p};
-                complete(S, one, AES_OK, it.launch_s, S->now());
-                worked = true;
-            }
             while (!S->rinflight[d].empty() && S->rinflight[d].front().done) {
                 const ResItem& f = S->rinflight[d].front();
                 S->rrel_tiles[d] = f.first_tile + f.ntiles;
                 S->rrel_items[d] = f.seq;
                 S->rinflight[d].pop_front();
             }
+        }
+        if (!finished.empty()) {  // one hand-over per pass, not one per request
+            {
+                std::lock_guard<std::mutex> lk(S->out_mu);
+                S->done.insert(S->done.end(), finished.begin(), finished.end());
+            }
+            {
+                std::lock_guard<std::mutex> lk(S->stats_mu);
+                S->stats.completed += finished.size();
+            }
+            S->finished.fetch_add(finished.size());
+            worked = true;
         }
         if (S->rlive) {  // has the kernel ended?
             int err = AES_OK;
@@ -655,7 +693,8 @@ static void scheduler_resident(aes_server* S) {
     // Shutdown: everything has completed and the kernel has been stopped.
 }
 
-static int enqueue(aes_server* S, const aes_server_request& r, double arrival) {
+// Checks one request on the host (sizes, key, pointers); AES_OK or the error it is refused with.
+static int check_request(aes_server* S, const aes_server_request& r) {
     if (r.key_index >= S->keys.size())
         return fail(AES_ERR_ARG, "request %llu: key_index %u >= %zu", (unsigned long long)r.id, r.key_index,
                     S->keys.size());
@@ -677,25 +716,41 @@ static int enqueue(aes_server* S, const aes_server_request& r, double arrival) {
     } else if (((uintptr_t)r.in | (uintptr_t)r.out) & 15u) {
         return fail(AES_ERR_ALIGN, "request %llu: pointers must be 16-byte aligned", (unsigned long long)r.id);
     }
-    S->submitted.fetch_add(1);
+    return AES_OK;
+}
+
+// Hands validated requests to the scheduler under one lock.
+static void push_inbox(aes_server* S, const Pending* p, size_t n) {
+    if (!n) return;
+    S->submitted.fetch_add(n);
     {
         std::lock_guard<std::mutex> lk(S->stats_mu);
-        S->stats.submitted++;
+        S->stats.submitted += n;
     }
     {
         std::lock_guard<std::mutex> lk(S->in_mu);
-        S->inbox.push_back(Pending{r, arrival});
+        S->inbox.insert(S->inbox.end(), p, p + n);
+        S->inbox_n.store(S->inbox.size(), std::memory_order_release);
     }
     S->in_cv.notify_one();
+}
+
+static int enqueue(aes_server* S, const aes_server_request& r, double arrival) {
+    const int rc = check_request(S, r);
+    if (rc) return rc;
+    const Pending p{r, arrival};
+    push_inbox(S, &p, 1);
     return AES_OK;
 }
 
 static void producer_main(aes_server* S) {
     const double start = S->now();
     S->replay_start = start;
-    for (const aes_server_request& r : S->replay_reqs) {
+    std::vector<Pending> due_now;
+    const size_t n = S->replay_reqs.size();
+    for (size_t i = 0; i < n;) {
         if (S->producer_stop.load()) break;
-        const double due = start + r.arrival_s;
+        const double due = start + S->replay_reqs[i].arrival_s;
         for (;;) {  // wait for the scheduled arrival time
             const double wait = due - S->now();
             if (wait <= 0) break;
@@ -706,12 +761,23 @@ static void producer_main(aes_server* S) {
             if (S->producer_stop.load()) break;
         }
         if (S->producer_stop.load()) break;
-        const int rc = enqueue(S, r, due);
-        if (rc != AES_OK) {  // rejected requests complete at once with their error
-            aes_server_completion c{r.id, rc, 0, due, due, S->now()};
-            std::lock_guard<std::mutex> lk(S->out_mu);
-            S->done.push_back(c);
+        // Every request already due goes over in one hand-over (under load the
+        // producer runs behind the schedule and several are due at once).
+        const double now = S->now();
+        due_now.clear();
+        for (; i < n && start + S->replay_reqs[i].arrival_s <= now; ++i) {
+            const aes_server_request& r = S->replay_reqs[i];
+            const double t = start + r.arrival_s;
+            const int rc = check_request(S, r);
+            if (rc == AES_OK) {
+                due_now.push_back(Pending{r, t});
+            } else {  // rejected requests complete at once with their error
+                aes_server_completion c{r.id, rc, 0, t, t, S->now()};
+                std::lock_guard<std::mutex> lk(S->out_mu);
+                S->done.push_back(c);
+            }
         }
+        push_inbox(S, due_now.data(), due_now.size());
     }
     S->producer_running.store(false);
 }
@@ -737,6 +803,7 @@ static void destroy_server(aes_server* S) {
         if (S->rargs.done) cudaFree(S->rargs.done);
         if (S->rargs.abandon) cudaFree(S->rargs.abandon);
         if (S->rargs.abandon_n) cudaFree(S->rargs.abandon_n);
+        if (S->rargs.cq_next) cudaFree(S->rargs.cq_next);
         if (S->rstream) cudaStreamDestroy(S->rstream);
     }
     delete S;
@@ -748,7 +815,8 @@ static bool pow2(uint32_t x) { return x && !(x & (x - 1)); }
 static int setup_resident(aes_server* S) {
     const aes_server_config& c = S->cfg;
     const uint32_t rt = c.ring_tiles, ri = c.ring_items;
-    const size_t bytes = sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt + sizeof(uint64_t) * 2 * (size_t)ri;
+    const uint32_t cq = 2 * ri;  // no more requests than this are in flight
+    const size_t bytes = sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt + sizeof(ResDone) * (size_t)cq;
     uint8_t* dev_view = nullptr;
     if (S->dryrun) {
         S->ring_mem = (uint8_t*)aligned_alloc(64, (bytes + 63) & ~(size_t)63);
@@ -766,6 +834,8 @@ static int setup_resident(aes_server* S) {
         if (e == cudaSuccess) e = cudaMalloc(&S->rargs.done, 2 * (size_t)ri * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMalloc(&S->rargs.abandon, 2 * (size_t)kAbandonCap * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMalloc(&S->rargs.abandon_n, 2 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&S->rargs.cq_next, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemset(S->rargs.cq_next, 0, sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMemset(S->rargs.abandon_n, 0, 2 * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMemset(S->rargs.claim, 0, 2 * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMemset(S->rargs.done, 0, 2 * (size_t)ri * sizeof(unsigned long long));
@@ -779,10 +849,11 @@ static int setup_resident(aes_server* S) {
     memset(S->ring_mem, 0, bytes);
     S->rctrl = (ResCtrl*)S->ring_mem;
     S->rtiles = (ResTile*)(S->ring_mem + sizeof(ResCtrl));
-    S->rstatus = (uint64_t*)(S->ring_mem + sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt);
+    S->rcq = (ResDone*)(S->ring_mem + sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt);
     S->rargs.ctrl = (const ResCtrl*)dev_view;
     S->rargs.tiles = (const ResTile*)(dev_view + sizeof(ResCtrl));
-    S->rargs.status = (uint64_t*)(dev_view + sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt);
+    S->rargs.cq = (ResDone*)(dev_view + sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt);
+    S->rargs.cq_size = cq;
     S->rargs.keys = S->dev_keys;
     S->rargs.err = S->status;
     S->rargs.ring_tiles = rt;
@@ -811,7 +882,7 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
     if (cfg.budget_bytes == 0) cfg.budget_bytes = (uint64_t)8 << 30;
     if (cfg.nstreams == 0) cfg.nstreams = 4;
     if (cfg.threads == 0) cfg.threads = 512;
-    if (cfg.blocks_per_thread == 0) cfg.blocks_per_thread = 1;
+    if (cfg.blocks_per_thread == 0) cfg.blocks_per_thread = (cfg.flags & AES_SERVER_RESIDENT) ? 2 : 1;
     if (cfg.max_batch_msgs == 0) cfg.max_batch_msgs = 4096;
     if (cfg.max_batch_blocks == 0) cfg.max_batch_blocks = (uint64_t)1 << 22;
     if (cfg.resident_idle_us == 0) cfg.resident_idle_us = 2000;
@@ -960,6 +1031,7 @@ int aes_server_cancel(aes_server* S, uint64_t id) {
     {
         std::lock_guard<std::mutex> lk(S->in_mu);
         S->cancels.push_back(id);
+        S->cancels_n.store(S->cancels.size(), std::memory_order_release);
     }
     S->in_cv.notify_one();
     return AES_OK;

@@ -16,7 +16,7 @@ GiB = 1 << 30
 
 
 def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8 << 30, nkeys: int = 1024,
-        nstreams: int = 4, threads: int = 0, blocks_per_thread: int = 1, max_batch_msgs: int = 4096,
+        nstreams: int = 4, threads: int = 0, blocks_per_thread: int = 0, max_batch_msgs: int = 4096,
         pool_bytes: int = GiB, check_last: int = 1000, seed: int = workloads.SEED_SERVE,
         resident: bool = False) -> dict:
     import torch
@@ -83,7 +83,7 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
         "mean_batch_msgs": float(n / max(1, len(batches))),
         ("kernel_launches" if resident else "batches"): int(stats["batches"]),
         "max_queue": int(stats["max_queue"]), "max_inflight_bytes": int(stats["max_inflight_bytes"]),
-        "budget_bytes": int(budget_bytes), "nstreams": nstreams, "shape": f"{threads or 512}x{blocks_per_thread}",
+        "budget_bytes": int(budget_bytes), "nstreams": nstreams, "shape": f"{threads or 512}x{blocks_per_thread or (2 if resident else 1)}",
         "checked_alone": int(len(idx)), "mismatches": mismatches,
         "workload": f"Poisson {rate:.0f} req/s for {duration_s:g} s, sizes log-uniform 64 B-1 MiB (x16 B), "
                     f"{nkeys} resident keys (128/192/256), encrypt/decrypt 50/50, {budget_bytes >> 30} GiB budget",

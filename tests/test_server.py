@@ -206,9 +206,9 @@ def test_resident_dryrun_idle_exit_and_relaunch(gbaes):
 def test_resident_config_errors(gbaes):
     with pytest.raises(gbaes.AesError):  # not a power of two
         gbaes.Server(keyset(gbaes), dryrun=True, resident=True, ring_tiles=100)
-    with pytest.raises(gbaes.AesError):  # the largest request (2^22 blocks) needs 8,192 tiles of 512
-        gbaes.Server(keyset(gbaes), dryrun=True, resident=True, ring_tiles=4096)
-    srv = gbaes.Server(keyset(gbaes), dryrun=True, resident=True, ring_tiles=4096, max_batch_blocks=4096 * 512)
+    with pytest.raises(gbaes.AesError):  # the largest request (2^22 blocks) needs 4,096 tiles of 512 x 2
+        gbaes.Server(keyset(gbaes), dryrun=True, resident=True, ring_tiles=2048)
+    srv = gbaes.Server(keyset(gbaes), dryrun=True, resident=True, ring_tiles=2048, max_batch_blocks=2048 * 1024)
     srv.close()
 
 
