@@ -719,7 +719,7 @@ def run_cpu_sweep():
 
 
 def run_serve_sweep(args):
-    """Open-loop serving at 200k, 400k, 800k and 1.6M requests/s (the serving
+    """Open-loop serving at 200k, 400k, 800k, 1.6M and 2.4M requests/s (the serving
     workload's sizes and keys), through the resident kernel and through launch
     per micro-batch: one JSON line per (mode, rate) with GB/s and latency
     percentiles."""
@@ -728,7 +728,7 @@ def run_serve_sweep(args):
     from paper_1201_0398_gb300 import load, serving
 
     load()
-    for rate in (200_000.0, 400_000.0, 800_000.0, 1_600_000.0):
+    for rate in (200_000.0, 400_000.0, 800_000.0, 1_600_000.0, 2_400_000.0):
         for resident in (True, False):
             r = serving.run(rate=rate, duration_s=args.serve_sweep_seconds, check_last=200, resident=resident)
             torch.cuda.empty_cache()

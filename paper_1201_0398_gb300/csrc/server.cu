@@ -533,7 +533,7 @@ static uint64_t request_tile_blocks(const aes_server* S, uint64_t n) {
 
 // Writes request p as tile records and publishes them.  Returns false if the
 // direction's ring has no room for it now.
-static bool publish(aes_server* S, const Pending& p, uint64_t bytes) {
+static bool publish(aes_server* S, const Pending& p, uint64_t bytes, double now) {
     const int d = (int)p.r.decrypt;
     const uint32_t rt = S->rargs.ring_tiles, ri = S->rargs.ring_items;
     const uint64_t tb = request_tile_blocks(S, p.r.nblocks);
@@ -553,7 +553,7 @@ static bool publish(aes_server* S, const Pending& p, uint64_t bytes) {
         R.item = slot;
         R.nr = (uint32_t)key.nr;
     }
-    ResItem it{p, seq, slot, S->rpub[d], ntiles, bytes, S->now(), false};
+    ResItem it{p, seq, slot, S->rpub[d], ntiles, bytes, now, false};
     S->rpub[d] += ntiles;
     S->rtiles_open += ntiles;
     __atomic_store_n(&S->rctrl->pub[d], S->rpub[d], __ATOMIC_RELEASE);  // records before the count
@@ -574,6 +574,7 @@ static void scheduler_resident(aes_server* S) {
         // reused only once it and every request before it in its direction
         // have finished).
         finished.clear();
+        const double pass_s = S->now();  // one clock read per pass, not per request
         for (;;) {
             const ResDone* e = &S->rcq[S->rcq_head & (S->rargs.cq_size - 1)];
             if (__atomic_load_n(&e->tag, __ATOMIC_ACQUIRE) != S->rcq_head + 1) break;
@@ -588,7 +589,7 @@ static void scheduler_resident(aes_server* S) {
             it.done = true;
             S->inflight_bytes -= it.bytes;
             S->rtiles_open -= it.ntiles;
-            finished.push_back(aes_server_completion{it.p.r.id, AES_OK, 1, it.p.arrival, it.launch_s, S->now()});
+            finished.push_back(aes_server_completion{it.p.r.id, AES_OK, 1, it.p.arrival, it.launch_s, pass_s});
         }
         for (int d = 0; d < 2; ++d) {
             while (!S->rinflight[d].empty() && S->rinflight[d].front().done) {
@@ -630,6 +631,8 @@ static void scheduler_resident(aes_server* S) {
             S->rstopping = true;
         }
         // Admission in arrival order while the budget and the ring have room.
+        const double admit_s = S->now();
+        size_t admitted = 0;
         while (!S->rstopping && !S->queue.empty()) {
             const Pending& p = S->queue.front();
             const uint64_t b = request_bytes(p.r);
@@ -651,19 +654,19 @@ static void scheduler_resident(aes_server* S) {
                 worked = true;
                 continue;
             }
-            if (!publish(S, p, b)) break;
+            if (!publish(S, p, b, admit_s)) break;
             ++S->batch_counter;
             S->inflight_bytes += b;
             S->queue.pop_front();
-            {
-                std::lock_guard<std::mutex> lk(S->stats_mu);
-                S->stats.max_inflight_bytes = std::max<uint64_t>(S->stats.max_inflight_bytes, S->inflight_bytes);
-                S->stats.max_batch_msgs = 1;
-            }
+            ++admitted;
             worked = true;
         }
         {
             std::lock_guard<std::mutex> lk(S->stats_mu);
+            if (admitted) {
+                S->stats.max_inflight_bytes = std::max<uint64_t>(S->stats.max_inflight_bytes, S->inflight_bytes);
+                S->stats.max_batch_msgs = 1;
+            }
             S->stats.max_queue = std::max<uint64_t>(S->stats.max_queue, S->queue.size());
         }
         inflight = !S->rinflight[0].empty() || !S->rinflight[1].empty();
