@@ -20,8 +20,15 @@
 //  * Latency is completion time minus arrival time (the scheduled arrival for
 //    replays, so a slow server cannot hide queueing delay).
 //
+// Resident mode (AES_SERVER_RESIDENT) replaces the per-batch launches: one
+// kernel (resident.cu) stays on the GPU, the scheduler publishes each admitted
+// request as tiles into a ring in page-locked memory and reads completions
+// from a completion queue there (protocol in resident.h), and it stops and
+// relaunches the kernel around idle periods.
+//
 // A dry-run mode replaces every CUDA call with a completion after a simulated
-// service time, so the scheduling logic (admission, budget, batching,
+// service time (in resident mode, a host thread that runs the kernel's
+// protocol), so the scheduling logic (admission, budget, batching, the ring,
 // cancellation, fault handling, drain) can be exercised without a GPU.
 #include <cuda_runtime.h>
 
