@@ -418,3 +418,57 @@ def test_resident_kernel_leaves_when_idle_and_is_relaunched(gbaes):
     assert launches == 2
     assert np.array_equal(y.cpu().numpy(), oracle.ecb(key, 128, x.cpu().numpy()))
     assert gbaes.device_status() == 0
+
+
+def test_resident_dryrun_ring_sized_requests(gbaes):
+    """Requests that need the whole tile ring (64 tiles of 64 blocks) alternate
+    with zero-length requests (which complete at once without touching the
+    ring) and single-block ones; all complete, in budget."""
+    srv = gbaes.Server(keyset(gbaes), dryrun=True, resident=True, threads=64, blocks_per_thread=1, ring_tiles=64,
+                       ring_items=4, max_batch_blocks=64 * 64)
+    ids = []
+    for i in range(60):
+        n = (64 * 64, 0, 1)[i % 3]
+        srv.submit(i, i % 4, 1 << 20, 2 << 20, n, bool(i & 1))
+        ids.append(i)
+    srv.drain(30.0)
+    done = srv.poll_all()
+    srv.close()
+    assert sorted(done["id"].tolist()) == ids and (done["status"] == 0).all()
+
+
+@pytest.mark.gpu
+def test_resident_ring_sized_zero_length_and_in_place(gbaes):
+    """On the GPU: requests that fill the whole (small) tile ring, zero-length
+    requests, and in-place requests of both directions on one buffer, through
+    one server; every output equals the oracle's."""
+    rng = np.random.default_rng(31)
+    key = rng.integers(0, 256, 24, dtype=np.uint8).tobytes()
+    k = gbaes.Key(key)
+    tile = 64 * 2  # 64 threads x 2 blocks
+    big = 16 * tile  # blocks: the whole ring of 16 tiles
+    data = rng.integers(0, 256, 16 * big * 4, dtype=np.uint8)
+    x = torch.from_numpy(data).cuda()
+    y = torch.zeros_like(x)
+    torch.cuda.synchronize()
+    srv = gbaes.Server([k], resident=True, threads=64, blocks_per_thread=2, ring_tiles=16, ring_items=4,
+                       max_batch_blocks=big)
+    for i in range(4):  # four ring-sized requests, x -> y
+        off = 16 * big * i
+        srv.submit(i, 0, x.data_ptr() + off, y.data_ptr() + off, big)
+        srv.submit(100 + i, 0, x.data_ptr(), y.data_ptr(), 0)  # zero-length
+    srv.drain(30.0)
+    for i in range(4):  # in place on y: decrypt halves 0 and 2, encrypt halves 1 and 3 again
+        off = 16 * big * i
+        srv.submit(10 + i, 0, y.data_ptr() + off, y.data_ptr() + off, big, bool(i % 2 == 0))
+    srv.drain(30.0)
+    done = srv.poll_all()
+    srv.close()
+    assert len(done) == 12 and (done["status"] == 0).all()
+    got = y.cpu().numpy().reshape(4, -1)
+    parts = data.reshape(4, -1)
+    for i in range(4):
+        c = oracle.ecb(key, 192, parts[i])
+        want = parts[i] if i % 2 == 0 else oracle.ecb(key, 192, c)
+        assert np.array_equal(got[i], want), i
+    assert gbaes.device_status() == 0
