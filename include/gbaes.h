@@ -265,6 +265,9 @@ typedef struct aes_server_config {
     uint32_t ring_tiles;           /* tile records per direction, a power of two (0 = 65536); must hold the
                                       largest request */
     uint32_t ring_items;           /* requests in flight per direction, a power of two (0 = 16384) */
+    uint32_t resident_restart_pct; /* the scheduler restarts the kernel at this % of its lifetime (0 = 80;
+                                      1..1000; above 100 the kernel's own bound ends it first, and the
+                                      scheduler recovers the tiles it left) */
 } aes_server_config;
 
 typedef struct aes_server_request {
@@ -292,6 +295,7 @@ typedef struct aes_server_stats {
     uint64_t max_queue;          /* peak requests waiting for admission */
     uint64_t max_batch_msgs;
     uint64_t budget_bytes;
+    uint64_t recovered_tiles;    /* resident mode: tiles re-published after the kernel's own bound ended it */
 } aes_server_stats;
 
 /* Creates a server on the current device with nkeys resident key contexts

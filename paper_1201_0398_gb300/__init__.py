@@ -430,12 +430,14 @@ class _ServerConfig(ctypes.Structure):
                 ("threads", ctypes.c_int32), ("blocks_per_thread", ctypes.c_int32), ("max_batch_msgs", ctypes.c_uint32),
                 ("dryrun_batch_us", ctypes.c_uint32), ("max_batch_blocks", ctypes.c_uint64),
                 ("resident_idle_us", ctypes.c_uint32), ("resident_lifetime_ms", ctypes.c_uint32),
-                ("ring_tiles", ctypes.c_uint32), ("ring_items", ctypes.c_uint32)]
+                ("ring_tiles", ctypes.c_uint32), ("ring_items", ctypes.c_uint32),
+                ("resident_restart_pct", ctypes.c_uint32)]
 
 
 class _ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "rejected", "batches",
-                                               "max_inflight_bytes", "max_queue", "max_batch_msgs", "budget_bytes")]
+                                               "max_inflight_bytes", "max_queue", "max_batch_msgs", "budget_bytes",
+                                               "recovered_tiles")]
 
 
 class Server:
@@ -446,13 +448,14 @@ class Server:
     def __init__(self, keys, budget_bytes: int = 8 << 30, nstreams: int = 4, threads: int = 0,
                  blocks_per_thread: int = 0, max_batch_msgs: int = 0, max_batch_blocks: int = 0, dryrun: bool = False,
                  dryrun_batch_us: int = 0, resident: bool = False, resident_idle_us: int = 0,
-                 resident_lifetime_ms: int = 0, ring_tiles: int = 0, ring_items: int = 0):
+                 resident_lifetime_ms: int = 0, ring_tiles: int = 0, ring_items: int = 0,
+                 resident_restart_pct: int = 0):
         self._lib = load()
         self._keys = list(keys)
         flags = (SERVER_DRYRUN if dryrun else 0) | (SERVER_RESIDENT if resident else 0)
         cfg = _ServerConfig(int(budget_bytes), int(nstreams), flags, int(threads), int(blocks_per_thread),
                             int(max_batch_msgs), int(dryrun_batch_us), int(max_batch_blocks), int(resident_idle_us),
-                            int(resident_lifetime_ms), int(ring_tiles), int(ring_items))
+                            int(resident_lifetime_ms), int(ring_tiles), int(ring_items), int(resident_restart_pct))
         h = self._lib.aes_server_create(_ctx_array(self._keys), len(self._keys), ctypes.byref(cfg))
         if not h:
             _check(-1)

@@ -358,7 +358,9 @@ static void scheduler_main(aes_server* S) {
 // kernel's ticket protocol (a ticket always held in its own direction, one in
 // the other when that has untaken published tiles), "enciphers" each tile for
 // dryrun_batch_us, counts blocks per request, publishes completions, and on
-// the stop word or its lifetime leaves, writing held tickets to the abandon list.
+// the stop word or its lifetime leaves, writing held tickets to the abandon
+// list (and, like a kernel whose last CTAs are still finishing, counting as
+// running for another 0.5 ms).
 static void fake_kernel_main(aes_server* S) {
     using clock = std::chrono::steady_clock;
     const clock::time_point start = clock::now();
@@ -386,6 +388,10 @@ static void fake_kernel_main(aes_server* S) {
                 if (published) continue;
                 for (int d = 0; d < 2; ++d)
                     if (held[d] != kNone) S->fake_abandon[d].push_back(held[d]);
+                // The kernel's CTAs leave one by one: the kernel still runs for
+                // a while after the first have abandoned their tickets, and the
+                // scheduler may publish those tiles meanwhile.
+                std::this_thread::sleep_for(std::chrono::microseconds(500));
                 break;
             }
             std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -465,6 +471,8 @@ static int recover_resident(aes_server* S) {
             if (S->rpub[d] + 1 - S->rrel_tiles[d] > rt) return fail(AES_ERR_STATE, "resident ring full during recovery");
             S->rtiles[(uint64_t)d * rt + (S->rpub[d] & (rt - 1))] = S->rtiles[(uint64_t)d * rt + (t & (rt - 1))];
             ++S->rpub[d];
+            std::lock_guard<std::mutex> lk(S->stats_mu);
+            S->stats.recovered_tiles++;
         }
         __atomic_store_n(&S->rctrl->pub[d], S->rpub[d], __ATOMIC_RELEASE);
     }
@@ -573,7 +581,8 @@ static void scheduler_resident(aes_server* S) {
     double last_work = S->now();
     std::vector<aes_server_completion> finished;
     const double idle_s = 1e-6 * S->cfg.resident_idle_us;
-    const double restart_s = 0.8e-3 * S->cfg.resident_lifetime_ms;  // well before the kernel's own bound
+    // Normally well before the kernel's own bound (80%); later in tests of the recovery.
+    const double restart_s = 1e-5 * S->cfg.resident_restart_pct * S->cfg.resident_lifetime_ms;
     for (;;) {
         bool worked = take_inbox(S);
         // Completions: new entries of the completion queue, in order.  Ring
@@ -899,9 +908,11 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
     if (cfg.resident_lifetime_ms == 0) cfg.resident_lifetime_ms = 10000;
     if (cfg.ring_tiles == 0) cfg.ring_tiles = 1u << 16;
     if (cfg.ring_items == 0) cfg.ring_items = 1u << 14;
+    if (cfg.resident_restart_pct == 0) cfg.resident_restart_pct = 80;
     if (cfg.nstreams < 1 || cfg.nstreams > 64 || cfg.threads < 64 || cfg.threads > 1024 || cfg.threads % 32 ||
         (cfg.blocks_per_thread != 1 && cfg.blocks_per_thread != 2 && cfg.blocks_per_thread != 4) ||
-        cfg.max_batch_msgs > (1u << 20) || (cfg.flags & ~(AES_SERVER_DRYRUN | AES_SERVER_RESIDENT))) {
+        cfg.max_batch_msgs > (1u << 20) || (cfg.flags & ~(AES_SERVER_DRYRUN | AES_SERVER_RESIDENT)) ||
+        cfg.resident_restart_pct > 1000) {
         fail(AES_ERR_ARG, "invalid server configuration");
         return nullptr;
     }

@@ -203,9 +203,30 @@ def test_resident_dryrun_idle_exit_and_relaunch(gbaes):
     srv.close()
 
 
+def test_resident_dryrun_recovery_after_kernel_bound(gbaes):
+    """The scheduler restarts the kernel only after its own lifetime bound has
+    ended it (restart at 1000% of a 3 ms lifetime), while requests keep
+    arriving: tiles published after the kernel left are recovered from its
+    abandoned tickets and re-published, and every request completes once."""
+    rng = np.random.default_rng(13)
+    srv = gbaes.Server(keyset(gbaes), dryrun=True, resident=True, resident_lifetime_ms=3, resident_restart_pct=1000)
+    reqs = fake_requests(gbaes, 20_000, rng, rate=100_000.0)  # ~0.2 s: dozens of kernel lifetimes
+    srv.replay(reqs)
+    srv.replay_join()
+    srv.drain(30.0)
+    done = srv.poll_all()
+    st = srv.stats()
+    srv.close()
+    assert sorted(done["id"].tolist()) == list(range(20_000)) and (done["status"] == 0).all()
+    assert st["batches"] >= 20  # kernel launches
+    assert st["recovered_tiles"] > 0  # the re-publishing path ran
+
+
 def test_resident_config_errors(gbaes):
     with pytest.raises(gbaes.AesError):  # not a power of two
         gbaes.Server(keyset(gbaes), dryrun=True, resident=True, ring_tiles=100)
+    with pytest.raises(gbaes.AesError):  # restart point above 1000% of the lifetime
+        gbaes.Server(keyset(gbaes), dryrun=True, resident=True, resident_restart_pct=1001)
     with pytest.raises(gbaes.AesError):  # the largest request (2^22 blocks) needs 4,096 tiles of 512 x 2
         gbaes.Server(keyset(gbaes), dryrun=True, resident=True, ring_tiles=2048)
     srv = gbaes.Server(keyset(gbaes), dryrun=True, resident=True, ring_tiles=2048, max_batch_blocks=2048 * 1024)
@@ -471,4 +492,41 @@ def test_resident_ring_sized_zero_length_and_in_place(gbaes):
         c = oracle.ecb(key, 192, parts[i])
         want = parts[i] if i % 2 == 0 else oracle.ecb(key, 192, c)
         assert np.array_equal(got[i], want), i
+    assert gbaes.device_status() == 0
+
+
+@pytest.mark.gpu
+def test_resident_recovery_after_kernel_bound(gbaes):
+    """On the GPU: the kernel's own 20 ms lifetime bound ends it while requests
+    keep arriving (the scheduler would restart it only at 1000%); the tickets
+    its CTAs abandoned are recovered and re-published.  Every output equals the
+    single-message kernel's and the oracle's on a sample."""
+    rng = np.random.default_rng(41)
+    nkeys = 16
+    bits = rng.choice([128, 192, 256], nkeys)
+    raw_keys = [rng.integers(0, 256, b // 8, dtype=np.uint8).tobytes() for b in bits]
+    keys = [gbaes.Key(k) for k in raw_keys]
+    reqs, x, y, in_off, out_off, lengths = device_requests(gbaes, rng, 6000, bits, 8 << 20, 64 << 10, 30_000.0)
+    torch.cuda.synchronize()
+    srv = gbaes.Server(keys, resident=True, resident_lifetime_ms=20, resident_restart_pct=1000)
+    srv.replay(reqs)  # ~0.2 s of arrivals: about ten kernel lifetimes
+    srv.replay_join()
+    srv.drain(60.0)
+    done = srv.poll_all()
+    st = srv.stats()
+    srv.close()
+    assert len(done) == len(reqs) and (done["status"] == 0).all()
+    assert st["batches"] >= 5
+    print("kernel launches", st["batches"], "recovered tiles", st["recovered_tiles"])
+    alone = torch.zeros_like(y)
+    for i in range(len(reqs)):
+        a, b, n = int(in_off[i]), int(out_off[i]), int(lengths[i])
+        gbaes.ecb_ex(keys[int(reqs["key_index"][i])], x[a:a + n], alone[b:b + n], decrypt=bool(reqs["decrypt"][i]))
+    torch.cuda.synchronize()
+    assert torch.equal(alone, y)
+    xs, ys = x.cpu().numpy(), y.cpu().numpy()
+    for i in rng.choice(len(reqs), 20, replace=False):
+        a, b, n = int(in_off[i]), int(out_off[i]), int(lengths[i])
+        k = int(reqs["key_index"][i])
+        assert np.array_equal(ys[b:b + n], oracle.ecb(raw_keys[k], int(bits[k]), xs[a:a + n], decrypt=bool(reqs["decrypt"][i])))
     assert gbaes.device_status() == 0
