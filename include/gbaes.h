@@ -136,7 +136,8 @@ typedef struct aes_batch_plan aes_batch_plan;
 /* Builds a reusable plan: validates every descriptor (AES_ERR_ARG /
  * AES_ERR_ALIGN), groups messages by direction and key size, tiles the
  * flattened blocks (one tile = 128 * blocks_per_thread blocks, taken by one
- * warp; CTAs of `threads` threads; 0, 0 = 1024, 2) and uploads the tile table, message table and every context's two
+ * warp; CTAs of `threads` threads; blocks_per_thread 1, 2, 4 or 8, with 8
+ * needing threads <= 512; 0, 0 = 1024, 2) and uploads the tile table, message table and every context's two
  * schedules to one device allocation on the current device (cudaMalloc,
  * synchronous).  msgs and ctxs are HOST arrays, read during the call only.
  * Returns NULL on error. */

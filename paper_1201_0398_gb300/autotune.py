@@ -18,7 +18,7 @@ import numpy as np
 from . import KERNEL_TABLE, BatchPlan, Key, ecb_ex, load, set_tuning
 
 ECB_CANDIDATES = [(1024, 1), (1024, 2), (1024, 4), (768, 2), (768, 4), (512, 2), (512, 4)]
-BATCH_CANDIDATES = [(1024, 2), (1024, 4), (1024, 1), (768, 2), (512, 4)]
+BATCH_CANDIDATES = [(1024, 2), (1024, 4), (1024, 1), (768, 2), (512, 4), (512, 8)]
 _lock = threading.Lock()
 
 

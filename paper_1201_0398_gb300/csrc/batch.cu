@@ -185,7 +185,7 @@ __device__ __forceinline__ GroupDev load_group(uint32_t gaddr, int g) {
 // The CTA meets at a barrier only to swap its shared-memory tables from the
 // encryption to the decryption set, once.
 template <int BPT>
-__global__ void __launch_bounds__(1024, 1) batch_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(BPT == 8 ? 512 : 1024, 1) batch_kernel(const BatchArgs a) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const uint32_t base = smem_base(smem_raw);
     const uint32_t A = table_base(base);
@@ -356,6 +356,7 @@ static BatchKernel pick_batch(int bpt) {
         case 1: return batch_kernel<1>;
         case 2: return batch_kernel<2>;
         case 4: return batch_kernel<4>;
+        case 8: return batch_kernel<8>;  // (512 threads at most: 128 registers per thread)
         default: return nullptr;
     }
 }
@@ -414,7 +415,8 @@ static unsigned batch_grid(uint32_t ntiles) {
 
 int launch_batch_kernel(const BatchArgs& a, int threads, int bpt, cudaStream_t stream) {
     BatchKernel fn = pick_batch(bpt);
-    if (!fn) return fail(AES_ERR_ARG, "blocks_per_thread %d: need 1, 2 or 4", bpt);
+    if (!fn) return fail(AES_ERR_ARG, "blocks_per_thread %d: need 1, 2, 4 or 8", bpt);
+    if (bpt == 8 && threads > 512) return fail(AES_ERR_ARG, "8 blocks per thread need threads <= 512");
     int smem = 0;
     int rc = batch_smem(fn, &smem);
     if (rc) return rc;
@@ -437,7 +439,11 @@ aes_batch_plan* aes_batch_plan_create(const aes_msg_desc* msgs, size_t nmsg, con
         return nullptr;
     }
     if (!pick_batch(blocks_per_thread)) {
-        fail(AES_ERR_ARG, "blocks_per_thread %d: need 1, 2 or 4", blocks_per_thread);
+        fail(AES_ERR_ARG, "blocks_per_thread %d: need 1, 2, 4 or 8", blocks_per_thread);
+        return nullptr;
+    }
+    if (blocks_per_thread == 8 && threads > 512) {
+        fail(AES_ERR_ARG, "8 blocks per thread need threads <= 512 (128 registers per thread)");
         return nullptr;
     }
     aes_batch_plan* P = new (std::nothrow) aes_batch_plan();

@@ -56,7 +56,7 @@ def main(argv=None):
         d = g.make_descs(off, off, w.lengths // 16, np.arange(len(ks)), w.decrypt)
         x = workloads.device_bytes(4, w.total_bytes)
         y = torch.empty_like(x)
-        plan = g.BatchPlan(d, ks, 1024, 4)
+        plan = g.BatchPlan(d, ks, 512, 8)
         plan.launch(x, y)
         for i in range(len(ks)):
             o, n = int(off[i]), int(w.lengths[i])
@@ -68,7 +68,7 @@ def main(argv=None):
         d = g.make_descs(off, off, w.lengths // 16, np.arange(len(ks)), w.decrypt)
         x = workloads.device_bytes(4, w.total_bytes)
         y = torch.empty_like(x)
-        plan = g.BatchPlan(d, ks, 1024, 4)
+        plan = g.BatchPlan(d, ks, 512, 8)
         for _ in range(a.warmup + a.launches):
             plan.launch(x, y)
     torch.cuda.synchronize()

@@ -52,6 +52,15 @@ def test_batch_tiles_match_model(gbaes):
         assert np.array_equal(got, model_tiles(nblocks, key_index, decrypt, bits, tb))
 
 
+def test_batch_plan_shape_errors(gbaes):
+    ks = [gbaes.Key(bytes(16))]
+    d = gbaes.make_descs([0], [0], [4], [0], [0])
+    for threads, bpt, text in ((1024, 8, "512"), (512, 3, "1, 2, 4 or 8"), (48, 2, "multiple of 32")):
+        with pytest.raises(gbaes.AesError) as e:
+            gbaes.BatchPlan(d, ks, threads, bpt)
+        assert text in str(e.value), (threads, bpt, str(e.value))
+
+
 def test_batch_descriptor_errors(gbaes):
     ks = [gbaes.Key(bytes(16))]
     bad_key = gbaes.make_descs([0], [0], [4], [1], [0])
@@ -94,7 +103,8 @@ def oracle_batch(data, keys, bits, nblocks, key_index, decrypt, in_off, out_off,
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("threads,bpt", [(1024, 2), (1024, 1), (1024, 4), (512, 2), (256, 4), (64, 1)])
+@pytest.mark.parametrize("threads,bpt", [(1024, 2), (1024, 1), (1024, 4), (512, 2), (256, 4), (64, 1), (512, 8),
+                                         (64, 8)])
 def test_batch_vs_oracle_and_single_kernel(gbaes, threads, bpt):
     rng = np.random.default_rng(threads + bpt)
     bits, keys, nblocks, key_index, decrypt = random_batch(rng, 400, 37, 5000)
