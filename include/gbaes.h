@@ -234,20 +234,19 @@ void aes_pipeline_free(aes_pipeline* pipe);
 /* Resident mode: instead of one batched-kernel launch per micro-batch, one
  * kernel stays on the GPU (one CTA per SM) and takes requests as they are
  * admitted.  The scheduler cuts each request into tiles of at most threads *
- * blocks_per_thread blocks (spread over up to one tile per SM, at least 256
- * blocks each), writes them into a ring in mapped page-locked memory and
- * publishes them with a release store; CTAs take tiles with tickets from an
- * atomic counter, and the CTA that finishes a request's last tile writes its
- * completion into a status word in page-locked memory, which the scheduler
- * polls.  No launch, copy or event per request.  The scheduler stops the
- * kernel after resident_idle_us without work and before resident_lifetime_ms
- * (its bound on the GPU) have passed, and relaunches it when work arrives;
- * while it runs it holds every SM, so other
- * kernels on the device wait for it, and so does a device-wide synchronisation
- * (cudaDeviceSynchronize).  Request inputs must be complete in
- * device memory when submitted.  With AES_SERVER_DRYRUN, a host thread runs
- * the kernel's protocol instead (each tile takes dryrun_batch_us).  Stats:
- * `batches` counts kernel launches, batch_msgs is 1. */
+ * blocks_per_thread blocks (spread over the idle CTAs, at least 256 blocks
+ * each), writes them into a ring in mapped page-locked memory and publishes
+ * them with a release store; CTAs take tiles with tickets from an atomic
+ * counter, and the CTA that finishes a request's last tile appends it to a
+ * completion queue in page-locked memory, which the scheduler reads.  No
+ * launch, copy or event per request.  The scheduler stops the kernel after
+ * resident_idle_us without work and before resident_lifetime_ms (its bound on
+ * the GPU) have passed, and relaunches it when work arrives.  While it runs it
+ * holds every SM, so other kernels on the device wait for it, and so does a
+ * device-wide synchronisation (cudaDeviceSynchronize).  Request inputs must be
+ * complete in device memory when submitted.  With AES_SERVER_DRYRUN, a host
+ * thread runs the kernel's protocol instead (each tile takes dryrun_batch_us).
+ * Stats: `batches` counts kernel launches, batch_msgs is 1. */
 #define AES_SERVER_RESIDENT 2
 
 typedef struct aes_server aes_server;

@@ -70,7 +70,7 @@ struct Slot {
 struct ResItem {
     Pending p;
     uint64_t seq;         // request number in its direction, from 1
-    uint32_t slot;        // its done counter and status word
+    uint32_t slot;        // its done counter on the device
     uint64_t first_tile;  // its tiles: [first_tile, first_tile + ntiles) of its direction
     uint64_t ntiles;
     uint64_t bytes;       // in+out bytes charged to the budget
