@@ -340,6 +340,36 @@ int aes_server_inject_fault(aes_server* server, uint64_t batch_index);
  * frees the server.  NULL is ignored. */
 void aes_server_destroy(aes_server* server);
 
+/* ---------------------------------------------------------------- routing
+ * Several servers behind one submission point: independent replicas (one
+ * server per GPU, each created with its device current) sharing nothing on
+ * the data path.  The router only chooses a server per request and merges
+ * their completions; it neither owns nor destroys the servers.  A resident
+ * server holds every SM of its GPU, so put one resident server per GPU. */
+
+#define AES_ROUTE_LEAST_LOADED 0 /* the server with the fewest unfinished requests (ties: round robin); every
+                                    server must be able to read the request's buffers */
+#define AES_ROUTE_BY_DEVICE 1    /* the least loaded of the servers on the device that holds the request's
+                                    input (input not in device memory, or no server there: of all) */
+
+typedef struct aes_router aes_router;
+
+/* servers: n >= 1 distinct servers (copied array).  NULL on error. */
+aes_router* aes_router_create(aes_server* const* servers, size_t n, int policy);
+
+/* Routes one request (aes_server_submit on the chosen server).  Returns the
+ * index of the chosen server (>= 0) or that server's error. */
+int aes_router_submit(aes_router* router, const aes_server_request* req);
+
+/* Moves up to max completions of every server into out; returns how many. */
+int aes_router_poll(aes_router* router, aes_server_completion* out, size_t max);
+
+/* aes_server_drain on every server with the same timeout. */
+int aes_router_drain(aes_router* router, double timeout_s);
+
+/* Frees the router (not the servers).  NULL is ignored. */
+void aes_router_destroy(aes_router* router);
+
 /* Default kernel variant for aes_encrypt_ecb / aes_decrypt_ecb (process-wide;
  * AES_KERNEL_TABLE at start).  Returns the previous variant or AES_ERR_ARG. */
 int aes_set_kernel(int which);

@@ -40,6 +40,9 @@ __all__ = [
     "Server",
     "SERVER_DRYRUN",
     "SERVER_RESIDENT",
+    "Router",
+    "ROUTE_LEAST_LOADED",
+    "ROUTE_BY_DEVICE",
     "REQUEST",
     "COMPLETION",
     "KERNEL_TABLE",
@@ -120,6 +123,11 @@ def _declare(lib):
         "aes_server_inject_fault": (c.c_int, [vp, c.c_uint64]),
         "aes_server_cancel": (c.c_int, [vp, c.c_uint64]),
         "aes_server_destroy": (None, [vp]),
+        "aes_router_create": (vp, [vp, sz, c.c_int]),
+        "aes_router_submit": (c.c_int, [vp, vp]),
+        "aes_router_poll": (c.c_int, [vp, vp, sz]),
+        "aes_router_drain": (c.c_int, [vp, c.c_double]),
+        "aes_router_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -512,3 +520,58 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+ROUTE_LEAST_LOADED = 0
+ROUTE_BY_DEVICE = 1
+
+
+class Router:
+    """Several servers (e.g. one per GPU) behind one submission point (aes_router).
+    The servers stay owned by the caller."""
+
+    def __init__(self, servers, policy: int = ROUTE_LEAST_LOADED):
+        self._lib = load()
+        self._servers = list(servers)
+        arr = (ctypes.c_void_p * len(self._servers))(*[srv._h for srv in self._servers])
+        h = self._lib.aes_router_create(arr, len(self._servers), int(policy))
+        if not h:
+            _check(-1)
+        self._h = ctypes.c_void_p(h)
+
+    def submit(self, req_id: int, key_index: int, in_ptr: int, out_ptr: int, nblocks: int,
+               decrypt: bool = False) -> int:
+        """Returns the index of the server the request went to."""
+        r = np.zeros(1, REQUEST)
+        r["id"], r["in_ptr"], r["out_ptr"], r["nblocks"] = req_id, in_ptr, out_ptr, nblocks
+        r["key_index"], r["decrypt"] = key_index, int(bool(decrypt))
+        return _check(self._lib.aes_router_submit(self._h, ctypes.c_void_p(r.ctypes.data)))
+
+    def drain(self, timeout_s: float = -1.0):
+        _check(self._lib.aes_router_drain(self._h, float(timeout_s)))
+
+    def poll(self, max_items: int = 1 << 22) -> np.ndarray:
+        out = np.zeros(max_items, COMPLETION)
+        n = _check(self._lib.aes_router_poll(self._h, ctypes.c_void_p(out.ctypes.data), max_items))
+        return out[:n]
+
+    def poll_all(self) -> np.ndarray:
+        parts = []
+        while True:
+            p = self.poll()
+            if p.size == 0:
+                break
+            parts.append(p)
+        return np.concatenate(parts) if parts else np.zeros(0, COMPLETION)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.aes_router_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

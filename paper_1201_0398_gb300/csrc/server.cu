@@ -1076,3 +1076,134 @@ void aes_server_destroy(aes_server* S) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ routing
+
+struct aes_router {
+    uint32_t magic = 0;
+    int policy = AES_ROUTE_LEAST_LOADED;
+    std::vector<aes_server*> servers;
+    std::mutex mu;       // the choice (and its round-robin cursor)
+    size_t next = 0;     // round-robin start among equally loaded servers
+    size_t poll_next = 0;
+};
+
+namespace gbaes {
+
+constexpr uint32_t kRouterMagic = 0x524f5554u;  // "ROUT"
+
+static bool valid_router(const aes_router* R) { return R && R->magic == kRouterMagic; }
+
+// Device that holds the memory at p (device or managed memory), else -1.
+static int device_of(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return -1;
+    return a.device;
+}
+
+}  // namespace gbaes
+
+extern "C" {
+
+aes_router* aes_router_create(aes_server* const* servers, size_t n, int policy) {
+    if (!servers || n == 0) {
+        fail(AES_ERR_ARG, "a router needs at least one server");
+        return nullptr;
+    }
+    if (policy != AES_ROUTE_LEAST_LOADED && policy != AES_ROUTE_BY_DEVICE) {
+        fail(AES_ERR_ARG, "unknown routing policy %d", policy);
+        return nullptr;
+    }
+    for (size_t i = 0; i < n; ++i) {
+        if (!servers[i] || servers[i]->magic != kServerMagic) {
+            fail(AES_ERR_ARG, "servers[%zu] is not a valid aes_server", i);
+            return nullptr;
+        }
+        for (size_t j = 0; j < i; ++j)
+            if (servers[j] == servers[i]) {
+                fail(AES_ERR_ARG, "servers[%zu] repeats servers[%zu]", i, j);
+                return nullptr;
+            }
+    }
+    aes_router* R = new (std::nothrow) aes_router();
+    if (!R) {
+        fail(AES_ERR_NOMEM, "out of host memory");
+        return nullptr;
+    }
+    R->policy = policy;
+    R->servers.assign(servers, servers + n);
+    R->magic = kRouterMagic;
+    return R;
+}
+
+int aes_router_submit(aes_router* R, const aes_server_request* r) {
+    if (!valid_router(R)) return fail(AES_ERR_ARG, "invalid aes_router");
+    if (!r) return fail(AES_ERR_ARG, "request is NULL");
+    const size_t n = R->servers.size();
+    size_t pick = n;
+    {
+        std::lock_guard<std::mutex> lk(R->mu);
+        // Candidates: the servers on the input's device (by-device policy),
+        // else every server.
+        int dev = -1;
+        if (R->policy == AES_ROUTE_BY_DEVICE && r->nblocks) {
+            dev = device_of(r->in);
+            bool any = false;
+            for (size_t i = 0; i < n && dev >= 0; ++i) any = any || (!R->servers[i]->dryrun && R->servers[i]->device == dev);
+            if (!any) dev = -1;
+        }
+        // The least loaded candidate (unfinished requests), round robin among ties.
+        uint64_t best = UINT64_MAX;
+        for (size_t k = 0; k < n; ++k) {
+            const size_t i = (R->next + k) % n;
+            const aes_server* S = R->servers[i];
+            if (dev >= 0 && (S->dryrun || S->device != dev)) continue;
+            const uint64_t load = S->submitted.load() - S->finished.load();
+            if (load < best) {
+                best = load;
+                pick = i;
+            }
+        }
+        R->next = (pick + 1) % n;
+    }
+    const int rc = aes_server_submit(R->servers[pick], r);
+    return rc == AES_OK ? (int)pick : rc;
+}
+
+int aes_router_poll(aes_router* R, aes_server_completion* out, size_t max) {
+    if (!valid_router(R)) return fail(AES_ERR_ARG, "invalid aes_router");
+    if (max && !out) return fail(AES_ERR_ARG, "out is NULL");
+    if (max > 0x7FFFFFFF) max = 0x7FFFFFFF;
+    size_t got = 0;
+    const size_t n = R->servers.size();
+    std::lock_guard<std::mutex> lk(R->mu);
+    for (size_t k = 0; k < n && got < max; ++k) {  // start where the last poll stopped: no server starves
+        const size_t i = (R->poll_next + k) % n;
+        const int m = aes_server_poll(R->servers[i], out + got, max - got);
+        if (m < 0) return m;
+        got += (size_t)m;
+    }
+    R->poll_next = (R->poll_next + 1) % n;
+    return (int)got;
+}
+
+int aes_router_drain(aes_router* R, double timeout_s) {
+    if (!valid_router(R)) return fail(AES_ERR_ARG, "invalid aes_router");
+    for (aes_server* S : R->servers) {
+        const int rc = aes_server_drain(S, timeout_s);
+        if (rc != AES_OK) return rc;
+    }
+    return AES_OK;
+}
+
+void aes_router_destroy(aes_router* R) {
+    if (!valid_router(R)) return;
+    R->magic = 0;
+    delete R;
+}
+
+}  // extern "C"
