@@ -98,16 +98,6 @@ __device__ __forceinline__ uint4 lds_v4(uint32_t addr) {
 
 constexpr unsigned long long kNoTicket = ~0ull;
 
-// One direction's share of a poll: takes a ticket when the CTA holds none in
-// this direction and either it is the CTA's own direction (so a ticket is
-// ready for the next tile published there) or the direction has published
-// tiles nobody has taken; then says whether the held ticket's tile is published.
-__device__ __forceinline__ bool poll_dir(const ResArgs& a, int d, bool own, uint64_t pub, unsigned long long claim,
-                                         unsigned long long& held) {
-    if (held == kNoTicket && (own || claim < pub)) held = atomicAdd(&a.claim[d], 1ull);
-    return held != kNoTicket && held < pub;
-}
-
 __device__ __forceinline__ void abandon_ticket(const ResArgs& a, int d, unsigned long long held) {
     if (held == kNoTicket) return;
     const unsigned long long i = atomicAdd(&a.abandon_n[d], 1ull);
@@ -121,50 +111,91 @@ __device__ __forceinline__ void load_pub(const ResArgs& a, uint64_t& p0, uint64_
     asm volatile("ld.relaxed.sys.global.v2.u64 {%0, %1}, [%2];" : "=l"(p0), "=l"(p1) : "l"(a.ctrl->pub) : "memory");
 }
 
+// The CTA's tickets (kept by thread 0 across tiles): held tile index per
+// direction (kNoTicket if none) and when the CTA first saw that tile published
+// (0: not yet).
+struct Tickets {
+    unsigned long long held[2];
+    uint64_t ready[2];
+};
+
+// A published ticket of the other direction waits at most this long while the
+// CTA keeps finding published tiles in its own direction.
+constexpr uint64_t kMaxHoldNs = 20000;
+
 // Thread 0: the next tile to encipher (true), or false when the CTA should
-// leave.  h0/h1: the tickets the CTA holds (kNoTicket if none), kept across
-// calls.  One poll issues the loads of both published counts, the stop word
-// and both ticket counters together (one host-link round trip); before a
-// published tile's record is read, an acquire fence orders the read after the
-// count that published it.  The CTA leaves on the stop word or its lifetime,
-// unless a held ticket's tile has been published (it enciphers that first).
-__device__ __forceinline__ bool next_tile(const ResArgs& a, int dir, uint64_t t_start, unsigned long long& h0,
-                                          unsigned long long& h1, int* tdir, uint64_t* tile) {
+// leave.  One poll issues the loads of both published counts, the stop word
+// and both ticket counters together (one host-link round trip).  The CTA
+// always holds a ticket in its table direction `dir` (taken before the tile is
+// published), and takes one in the other direction when that direction has
+// published tiles nobody has taken.  It enciphers its own direction's tile
+// when published, unless the other direction's held tile has been published
+// for kMaxHoldNs (without that bound, a steady stream of own-direction work
+// would starve it).  Before a tile's record is read, an acquire fence orders
+// the read after the count that published it.  The CTA leaves on the stop
+// word or its lifetime, unless a held ticket's tile has been published (it
+// enciphers that first).
+__device__ __forceinline__ bool next_tile(const ResArgs& a, int dir, uint64_t t_start, Tickets& tk, int* tdir,
+                                          uint64_t* tile) {
+    const int oth = dir ^ 1;
     for (;;) {
-        const uint64_t now = globaltimer_ns();
-        uint64_t p0, p1;
-        load_pub(a, p0, p1);
+        const uint64_t now = globaltimer_ns() | 1u;  // (never 0: 0 marks "not seen published")
+        uint64_t pub[2];
+        load_pub(a, pub[0], pub[1]);
         const uint32_t stop = ld_volatile_u32(&a.ctrl->stop);
-        const unsigned long long c0 = ld_volatile_u64(&a.claim[0]), c1 = ld_volatile_u64(&a.claim[1]);
+        const unsigned long long claim_oth = ld_volatile_u64(&a.claim[oth]);
+        // Own / other direction views, by selects (no run-time index into a local array).
+        const uint64_t pub_own = dir ? pub[1] : pub[0], pub_oth = dir ? pub[0] : pub[1];
+        unsigned long long h_own = dir ? tk.held[1] : tk.held[0], h_oth = dir ? tk.held[0] : tk.held[1];
+        uint64_t r_own = dir ? tk.ready[1] : tk.ready[0], r_oth = dir ? tk.ready[0] : tk.ready[1];
+        if (h_own == kNoTicket) {
+            h_own = atomicAdd(&a.claim[dir], 1ull);
+            r_own = 0;
+        }
+        if (h_oth == kNoTicket && claim_oth < pub_oth) {
+            h_oth = atomicAdd(&a.claim[oth], 1ull);
+            r_oth = 0;
+        }
+        const bool own_ready = h_own < pub_own;
+        const bool oth_ready = h_oth != kNoTicket && h_oth < pub_oth;
+        if (own_ready && !r_own) r_own = now;
+        if (oth_ready && !r_oth) r_oth = now;
         int got = -1;
-        if (dir == 0) {
-            if (poll_dir(a, 0, true, p0, c0, h0))
-                got = 0;
-            else if (poll_dir(a, 1, false, p1, c1, h1))
-                got = 1;
+        if (oth_ready && (!own_ready || now - r_oth > kMaxHoldNs))
+            got = oth;
+        else if (own_ready)
+            got = dir;
+        if (got == oth) {
+            *tile = h_oth;
+            h_oth = kNoTicket;
+            r_oth = 0;
+        } else if (got == dir) {
+            *tile = h_own;
+            h_own = kNoTicket;
+            r_own = 0;
+        }
+        if (dir) {
+            tk.held[1] = h_own;
+            tk.held[0] = h_oth;
+            tk.ready[1] = r_own;
+            tk.ready[0] = r_oth;
         } else {
-            if (poll_dir(a, 1, true, p1, c1, h1))
-                got = 1;
-            else if (poll_dir(a, 0, false, p0, c0, h0))
-                got = 0;
+            tk.held[0] = h_own;
+            tk.held[1] = h_oth;
+            tk.ready[0] = r_own;
+            tk.ready[1] = r_oth;
         }
         if (got >= 0) {
             asm volatile("fence.acq_rel.sys;" ::: "memory");
             *tdir = got;
-            if (got) {
-                *tile = h1;
-                h1 = kNoTicket;
-            } else {
-                *tile = h0;
-                h0 = kNoTicket;
-            }
             return true;
         }
         if (stop || now - t_start > a.lifetime_ns) {
-            load_pub(a, p0, p1);  // fresh counts: a held tile published since the poll is enciphered first
-            if ((h0 != kNoTicket && h0 < p0) || (h1 != kNoTicket && h1 < p1)) continue;
-            abandon_ticket(a, 0, h0);
-            abandon_ticket(a, 1, h1);
+            load_pub(a, pub[0], pub[1]);  // fresh counts: a held tile published since the poll is enciphered first
+            if ((tk.held[0] != kNoTicket && tk.held[0] < pub[0]) || (tk.held[1] != kNoTicket && tk.held[1] < pub[1]))
+                continue;
+            abandon_ticket(a, 0, tk.held[0]);
+            abandon_ticket(a, 1, tk.held[1]);
             return false;
         }
         __nanosleep(200);
@@ -192,13 +223,13 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(const ResArgs a) {
     int dir = (int)(blockIdx.x & 1u);
     fill_tables(A, dir != 0);
     const uint64_t t_start = globaltimer_ns();
-    unsigned long long h0 = kNoTicket, h1 = kNoTicket;  // thread 0's tickets
+    Tickets tk{{kNoTicket, kNoTicket}, {0, 0}};  // thread 0's tickets
     for (;;) {
         if (threadIdx.x == 0) {
             int tdir = dir;
             uint64_t tile = 0;
             uint32_t cmd = 1;
-            if (next_tile(a, dir, t_start, h0, h1, &tdir, &tile)) {
+            if (next_tile(a, dir, t_start, tk, &tdir, &tile)) {
                 const uint8_t* rec = (const uint8_t*)(a.tiles + (uint64_t)tdir * a.ring_tiles + (tile & (a.ring_tiles - 1)));
 #pragma unroll
                 for (int q = 0; q < 3; ++q) sts_v4(ctl + 16u * q, ld_volatile_v4(rec + 16 * q));

@@ -106,7 +106,10 @@ struct aes_server {
     uint64_t batch_counter = 0;   // scheduler thread only
 
     std::mutex out_mu;
-    std::vector<aes_server_completion> done;
+    // Completions waiting for aes_server_poll.  A deque: it grows without copying what it holds (a vector's
+    // reallocation copied hundreds of MB under out_mu and stalled the scheduler for tens of ms) and
+    // releases from the front.
+    std::deque<aes_server_completion> done;
 
     std::mutex stats_mu;
     aes_server_stats stats{};
@@ -356,7 +359,8 @@ static void scheduler_main(aes_server* S) {
 
 // Dry-run stand-in for the resident kernel: one host thread follows the
 // kernel's ticket protocol (a ticket always held in its own direction, one in
-// the other when that has untaken published tiles), "enciphers" each tile for
+// the other when that has untaken published tiles; own direction first unless
+// the other's tile has waited 20 us), "enciphers" each tile for
 // dryrun_batch_us, counts blocks per request, publishes completions, and on
 // the stop word or its lifetime leaves, writing held tickets to the abandon
 // list (and, like a kernel whose last CTAs are still finishing, counting as
@@ -367,16 +371,35 @@ static void fake_kernel_main(aes_server* S) {
     const uint32_t rt = S->rargs.ring_tiles, ri = S->rargs.ring_items;
     constexpr uint64_t kNone = ~0ull;
     uint64_t held[2] = {kNone, kNone};
+    clock::time_point ready[2];  // first seen published
+    bool seen[2] = {false, false};
     int dir = 0;
     for (;;) {
         uint64_t pub[2] = {__atomic_load_n(&S->rctrl->pub[0], __ATOMIC_ACQUIRE),
                            __atomic_load_n(&S->rctrl->pub[1], __ATOMIC_ACQUIRE)};
-        int got = -1;
-        for (int k = 0; k < 2 && got < 0; ++k) {
-            const int d = k ? dir ^ 1 : dir;
-            if (held[d] == kNone && (k == 0 || S->fake_claim[d] < pub[d])) held[d] = S->fake_claim[d]++;
-            if (held[d] != kNone && held[d] < pub[d]) got = d;
+        const int oth = dir ^ 1;
+        if (held[dir] == kNone) {
+            held[dir] = S->fake_claim[dir]++;
+            seen[dir] = false;
         }
+        if (held[oth] == kNone && S->fake_claim[oth] < pub[oth]) {
+            held[oth] = S->fake_claim[oth]++;
+            seen[oth] = false;
+        }
+        const clock::time_point t = clock::now();
+        bool ok[2];
+        for (int d = 0; d < 2; ++d) {
+            ok[d] = held[d] != kNone && held[d] < pub[d];
+            if (ok[d] && !seen[d]) {
+                seen[d] = true;
+                ready[d] = t;
+            }
+        }
+        int got = -1;  // own direction first, unless the other's tile has waited 20 us
+        if (ok[oth] && (!ok[dir] || t - ready[oth] > std::chrono::microseconds(20)))
+            got = oth;
+        else if (ok[dir])
+            got = dir;
         if (got < 0) {
             const bool expired = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(clock::now() - start)
                                      .count() > S->rargs.lifetime_ns;
@@ -400,6 +423,7 @@ static void fake_kernel_main(aes_server* S) {
         dir = got;
         const ResTile R = S->rtiles[(uint64_t)got * rt + (held[got] & (rt - 1))];
         held[got] = kNone;
+        seen[got] = false;
         if (S->cfg.dryrun_batch_us) std::this_thread::sleep_for(std::chrono::microseconds(S->cfg.dryrun_batch_us));
         uint64_t& done = S->fake_done[(uint64_t)got * ri + R.item];
         done += R.nblocks;
