@@ -794,12 +794,12 @@ static void producer_main(aes_server* S) {
     for (size_t i = 0; i < n;) {
         if (S->producer_stop.load()) break;
         const double due = start + S->replay_reqs[i].arrival_s;
-        for (;;) {  // wait for the scheduled arrival time
+        for (;;) {  // wait for the scheduled arrival time: sleep, then yield, then spin for the last 50 us
             const double wait = due - S->now();
             if (wait <= 0) break;
             if (wait > 200e-6)
                 std::this_thread::sleep_for(std::chrono::duration<double>(wait - 100e-6));
-            else
+            else if (wait > 50e-6)
                 std::this_thread::yield();
             if (S->producer_stop.load()) break;
         }
