@@ -602,7 +602,7 @@ static bool publish(aes_server* S, const Pending& p, uint64_t bytes, double now)
 
 static void scheduler_resident(aes_server* S) {
     if (!S->dryrun) cudaSetDevice(S->device);
-    double last_work = S->now();
+    double last_work = S->now(), last_query = 0;
     std::vector<aes_server_completion> finished;
     const double idle_s = 1e-6 * S->cfg.resident_idle_us;
     // Normally well before the kernel's own bound (80%); later in tests of the recovery.
@@ -651,7 +651,11 @@ static void scheduler_resident(aes_server* S) {
             S->finished.fetch_add(finished.size());
             worked = true;
         }
-        if (S->rlive) {  // has the kernel ended?
+        // Has the kernel ended?  (A driver query: on every pass while it is
+        // stopping, else every 50 us -- it ends on its own only at its lifetime
+        // bound or on a fault, and the query would lengthen every pass.)
+        if (S->rlive && (S->rstopping || pass_s - last_query > 50e-6)) {
+            last_query = pass_s;
             int err = AES_OK;
             if (!resident_running(S, &err)) {
                 S->rlive = false;
@@ -791,8 +795,23 @@ static void producer_main(aes_server* S) {
     S->replay_start = start;
     std::vector<Pending> due_now;
     const size_t n = S->replay_reqs.size();
+    // Hands request r (already checked: rc) to the scheduler's batch, or
+    // completes it at once with its error.
+    auto take = [&](const aes_server_request& r, int rc) {
+        const double t = start + r.arrival_s;
+        if (rc == AES_OK) {
+            due_now.push_back(Pending{r, t});
+        } else {
+            aes_server_completion c{r.id, rc, 0, t, t, S->now()};
+            std::lock_guard<std::mutex> lk(S->out_mu);
+            S->done.push_back(c);
+        }
+    };
     for (size_t i = 0; i < n;) {
         if (S->producer_stop.load()) break;
+        // The next request is checked before its arrival time, so the driver
+        // queries of the check are not part of its latency.
+        const int rc_first = check_request(S, S->replay_reqs[i]);
         const double due = start + S->replay_reqs[i].arrival_s;
         for (;;) {  // wait for the scheduled arrival time: sleep, then yield, then spin for the last 50 us
             const double wait = due - S->now();
@@ -806,20 +825,11 @@ static void producer_main(aes_server* S) {
         if (S->producer_stop.load()) break;
         // Every request already due goes over in one hand-over (under load the
         // producer runs behind the schedule and several are due at once).
-        const double now = S->now();
         due_now.clear();
-        for (; i < n && start + S->replay_reqs[i].arrival_s <= now; ++i) {
-            const aes_server_request& r = S->replay_reqs[i];
-            const double t = start + r.arrival_s;
-            const int rc = check_request(S, r);
-            if (rc == AES_OK) {
-                due_now.push_back(Pending{r, t});
-            } else {  // rejected requests complete at once with their error
-                aes_server_completion c{r.id, rc, 0, t, t, S->now()};
-                std::lock_guard<std::mutex> lk(S->out_mu);
-                S->done.push_back(c);
-            }
-        }
+        take(S->replay_reqs[i++], rc_first);
+        const double now = S->now();
+        for (; i < n && start + S->replay_reqs[i].arrival_s <= now; ++i)
+            take(S->replay_reqs[i], check_request(S, S->replay_reqs[i]));
         push_inbox(S, due_now.data(), due_now.size());
     }
     S->producer_running.store(false);
