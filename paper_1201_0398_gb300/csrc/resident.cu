@@ -280,20 +280,26 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(const ResArgs a) {
             const uint64_t item_blocks = ((uint64_t)r1.y << 32) | r1.x;
             const uint64_t seq = ((uint64_t)r1.w << 32) | r1.z;
             const uint64_t slot = (uint64_t)dir * a.ring_items + r2.z;
-            // Release: the CTA's outputs (fenced by every thread, then the
-            // barrier) before the count; acquire: the outputs of the tiles
-            // counted before it.
-            unsigned long long before;
-            asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
-                         : "=l"(before)
-                         : "l"(a.done + slot), "l"((unsigned long long)n)
-                         : "memory");
-            if (before + n == item_blocks) {  // the request's last tile: every other tile was counted before
-                // No other CTA touches the counter now.  The entry's tag is
-                // written last with a release store: it orders the reset, the
-                // entry and every output this thread has acquired before it;
-                // after it the host may reuse the request's slot.
-                asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(a.done + slot), "l"(0ull) : "memory");
+            // A request of one tile is complete now: no count.  Otherwise the
+            // count -- release: the CTA's outputs (fenced by every thread, then
+            // the barrier) before it; acquire: the outputs of the tiles counted
+            // before it.
+            bool last = n == item_blocks;
+            if (!last) {
+                unsigned long long before;
+                asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
+                             : "=l"(before)
+                             : "l"(a.done + slot), "l"((unsigned long long)n)
+                             : "memory");
+                last = before + n == item_blocks;  // every other tile was counted before
+                // No other CTA touches the counter now: reset it for the slot's next request.
+                if (last) asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(a.done + slot), "l"(0ull) : "memory");
+            }
+            if (last) {
+                // The entry's tag is written last with a release store: it
+                // orders the reset, the entry and every output this thread has
+                // acquired (or its CTA wrote) before it; after it the host may
+                // reuse the request's slot.
                 const unsigned long long i = atomicAdd(a.cq_next, 1ull);
                 ResDone* e = a.cq + (i & (a.cq_size - 1));
                 asm volatile("st.relaxed.sys.global.u64 [%0], %1;" ::"l"(&e->what),
