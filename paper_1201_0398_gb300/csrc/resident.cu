@@ -261,13 +261,31 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(const ResArgs a) {
         }
         if (threadIdx.x <= nr) sts_v4(kslot + 16u * threadIdx.x, __ldg(a.keys + (uint64_t)key_slot * 16u + threadIdx.x));
         __syncthreads();  // the tables (after a swap) and the key slot are in place
-        // Warps past the tile's last block skip the rounds: their lookups would
-        // take shared-memory cycles from the warps that have blocks.
+        // Warps past the tile's last block skip the rounds, and every thread
+        // runs only as many states as the tile fills (thread i has blocks i,
+        // i + threads, ...): lookups on empty states would take shared-memory
+        // cycles from the blocks that exist.  Small tiles thus cost what they
+        // would with one block per thread, full ones amortise the tile's
+        // fixed costs over BPT blocks per thread.
         if ((threadIdx.x & ~31u) < n) {
-            if (dir)
+            const uint32_t states = (n + blockDim.x - 1) / blockDim.x;  // 1..BPT, the same in every thread
+            if (states <= 1) {
+                uint32_t(&s1)[1][4] = *reinterpret_cast<uint32_t(*)[1][4]>(&s[0]);
+                if (dir)
+                    cipher_rt<true, 1>(s1, SmemKeys{kslot}, (int)nr, L0, L1);
+                else
+                    cipher_rt<false, 1>(s1, SmemKeys{kslot}, (int)nr, L0, L1);
+            } else if (BPT >= 4 && states <= 2) {
+                uint32_t(&s2)[2][4] = *reinterpret_cast<uint32_t(*)[2][4]>(&s[0]);
+                if (dir)
+                    cipher_rt<true, 2>(s2, SmemKeys{kslot}, (int)nr, L0, L1);
+                else
+                    cipher_rt<false, 2>(s2, SmemKeys{kslot}, (int)nr, L0, L1);
+            } else if (dir) {
                 cipher_rt<true, BPT>(s, SmemKeys{kslot}, (int)nr, L0, L1);
-            else
+            } else {
                 cipher_rt<false, BPT>(s, SmemKeys{kslot}, (int)nr, L0, L1);
+            }
         }
 #pragma unroll
         for (int b = 0; b < BPT; ++b) {
