@@ -82,6 +82,10 @@ def parse_args():
     p.add_argument("--serve-sweep", action="store_true",
                    help="serving latency against offered load (both server modes), one JSON line per point")
     p.add_argument("--serve-sweep-seconds", type=float, default=2.0)
+    p.add_argument("--profile-case", choices=PROFILE_CASES,
+                   help="run one small fixed case for an ncu capture (no timing, no JSON line)")
+    p.add_argument("--profile-warmup", type=int, default=2)
+    p.add_argument("--profile-launches", type=int, default=3)
     return p.parse_args()
 
 
@@ -739,8 +743,75 @@ def run_serve_sweep(args):
                               **{k: r[k] for k in keep if k in r}}), flush=True)
 
 
+PROFILE_CASES = ("table", "table1g", "bitsliced", "batch", "sweep", "singles")
+
+
+def run_profile_case(args):
+    """Small fixed cases for profiling one kernel at a time (ncu -k ... -s W -c N).
+
+    Each case runs --profile-warmup launches then --profile-launches more of one
+    kernel, on inputs larger than the 129 MB L2 but a few hundred MB in all (so a
+    multi-pass capture ends in seconds), except table1g:
+      table      256 MiB, AES-128 encryption + AES-256 decryption, table kernel
+      table1g    1 GiB, the bench's launches (AES-128/192/256, encrypt + decrypt),
+                 for single-pass DRAM-byte captures at the bench size only
+      bitsliced  64 MiB, AES-128 encryption + decryption, bitsliced kernel
+      batch      10,000 messages, 16 B - 1 MiB (~0.95 GB), one batched launch each
+      sweep      one AES-128 encryption per size, 4 KiB - 1 GiB, table then bitsliced
+      singles    the 10,000-message batch as one batched launch, then as 10,000
+                 single-message launches
+    """
+    import numpy as np
+    import torch
+
+    import paper_1201_0398_gb300 as g
+    from paper_1201_0398_gb300 import workloads
+
+    g.load()
+    case, warm, launches = args.profile_case, args.profile_warmup, args.profile_launches
+    if case in ("table", "table1g", "bitsliced"):
+        kid = g.KERNEL_BITSLICED if case == "bitsliced" else g.KERNEL_TABLE
+        size = {"table": 256 << 20, "table1g": GiB, "bitsliced": 64 << 20}[case]
+        ops = {"table": [(128, False), (256, True)], "bitsliced": [(128, False), (128, True)],
+               "table1g": [(b, d) for b in BITS for d in (False, True)]}[case]
+        x = workloads.device_bytes(1, size)
+        y = torch.empty_like(x)
+        keys = {b: g.Key(workloads.random_key(b, b)) for b, _ in ops}
+        for _ in range(warm + launches):
+            for bits, dec in ops:
+                g.ecb_ex(keys[bits], x, y, decrypt=dec, kernel=kid)
+    elif case == "sweep":
+        x = workloads.device_bytes(31, GiB)
+        y = torch.empty_like(x)
+        k = g.Key(workloads.random_key(168, 128))
+        for kid in (g.KERNEL_TABLE, g.KERNEL_BITSLICED):
+            for size in (4096 * 4 ** i for i in range(10)):  # 4 KiB .. 1 GiB
+                g.ecb_ex(k, x[:size], y[:size], kernel=kid)
+    else:
+        w = workloads.batch_workload(n=10000, max_len=MiB) if case == "batch" else workloads.batch_workload()
+        ks = [g.Key(k) for k in w.keys]
+        off = np.concatenate([[0], np.cumsum(w.lengths)[:-1]])
+        d = g.make_descs(off, off, w.lengths // 16, np.arange(len(ks)), w.decrypt)
+        x = workloads.device_bytes(4, w.total_bytes)
+        y = torch.empty_like(x)
+        plan = g.BatchPlan(d, ks, 512, 8)
+        if case == "batch":
+            for _ in range(warm + launches):
+                plan.launch(x, y)
+        else:
+            plan.launch(x, y)
+            for i in range(len(ks)):
+                o, n = int(off[i]), int(w.lengths[i])
+                g.ecb_ex(ks[i], x[o:o + n], y[o:o + n], decrypt=bool(w.decrypt[i]))
+    torch.cuda.synchronize()
+    print(f"profile case {case}: ok", file=sys.stderr)
+
+
 def main():
     args = parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.serve_sweep:
         run_serve_sweep(args)
         return

@@ -166,7 +166,10 @@ void aes_batch_plan_free(aes_batch_plan* plan);
 
 /* One-shot batch: plan tables in stream-ordered scratch (cudaMallocAsync /
  * cudaFreeAsync on `stream`), one launch with 1024 threads x 2 blocks per
- * tile.  Same arguments and rules as the plan calls. */
+ * tile.  Same arguments and rules as the plan calls.  The tables are uploaded
+ * from a host copy that is freed when the call returns, so a stream that is
+ * being captured into a CUDA graph is refused (AES_ERR_STATE); for graphs use
+ * a plan and aes_batch_plan_launch_graph. */
 int aes_ecb_batch(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx, const void* in_base,
                   size_t in_bytes, void* out_base, size_t out_bytes, void* stream);
 
@@ -181,9 +184,9 @@ int aes_ecb_batch(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* c
  *  - A batch whose tables exceed 8 MiB (512 bytes per key context, 32 bytes per
  *    message, 4 bytes per 2048-block tile, plus 256) is rejected with
  *    AES_ERR_ARG; the 10,000-message, 10,000-key batch needs about 5.6 MiB.
- *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *  - The first call in each CUDA context (normally once per device, in its
+ *    primary context) looks up the array's device address there
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
  *  - Every call shares the one array and overwrites it (the tile counter is
  *    re-zeroed by each call's upload).  Calls whose work overlaps on the GPU
  *    -- on different streams, or from different host threads -- race on it;

@@ -7,6 +7,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <set>
+#include <utility>
 
 #include "aes_tables.h"
 #include "gbaes_internal.h"
@@ -114,16 +116,71 @@ int current_device_info(DeviceInfo* info) {
     return AES_OK;
 }
 
+// The CUDA context current on this thread, as an id that is unique for the
+// process's life (a handle value can be reused once a context is destroyed, an
+// id cannot).  Per-context state -- a kernel's shared-memory attribute, the
+// device address of a __device__ symbol -- belongs to the module loaded in one
+// context, so it is cached by this id, not by device index: a caller may make
+// its own context current, and cudaDeviceReset replaces the primary context.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+static CtxGetCurrentFn g_ctx_current = nullptr;
+static CtxGetIdFn g_ctx_get_id = nullptr;
+static bool g_ctx_fns_tried = false;
+
+static void* driver_fn(const char* name) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        return fn;
+    return nullptr;
+}
+
+int current_context_id(unsigned long long* id) {
+    {
+        std::lock_guard<std::mutex> lk(g_dev_mu);
+        if (!g_ctx_fns_tried) {
+            g_ctx_fns_tried = true;
+            g_ctx_current = (CtxGetCurrentFn)driver_fn("cuCtxGetCurrent");
+            g_ctx_get_id = (CtxGetIdFn)driver_fn("cuCtxGetId");
+        }
+    }
+    if (!g_ctx_current || !g_ctx_get_id) return fail(AES_ERR_CUDA, "cuCtxGetCurrent/cuCtxGetId unavailable");
+    CUcontext c = nullptr;
+    if (g_ctx_current(&c) != CUDA_SUCCESS) return fail(AES_ERR_CUDA, "cuCtxGetCurrent failed");
+    if (!c) {
+        // Nothing current yet: cudaSetDevice makes the device's primary context
+        // current (it allocates nothing).
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaSetDevice(dev);
+        if (e != cudaSuccess) return fail(AES_ERR_CUDA, "no CUDA context: %s", cudaGetErrorString(e));
+        if (g_ctx_current(&c) != CUDA_SUCCESS || !c) return fail(AES_ERR_CUDA, "no current CUDA context");
+    }
+    if (g_ctx_get_id(c, id) != CUDA_SUCCESS) return fail(AES_ERR_CUDA, "cuCtxGetId failed");
+    return AES_OK;
+}
+
+int set_max_dynamic_smem(const void* fn, int bytes) {
+    unsigned long long ctx = 0;
+    int rc = current_context_id(&ctx);
+    if (rc) return rc;
+    static std::mutex mu;
+    static std::set<std::pair<const void*, unsigned long long>> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({fn, ctx})) return AES_OK;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    done.insert({fn, ctx});
+    return AES_OK;
+}
+
 static PointerAttrsFn pointer_attrs_fn() {
     std::lock_guard<std::mutex> lk(g_dev_mu);
     if (!g_ptr_attrs_tried) {
         g_ptr_attrs_tried = true;
-        void* fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttributes", &fn, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            g_ptr_attrs = (PointerAttrsFn)fn;
+        g_ptr_attrs = (PointerAttrsFn)driver_fn("cuPointerGetAttributes");
     }
     return g_ptr_attrs;
 }

@@ -390,19 +390,13 @@ static int plan_launch_args(aes_batch_plan* P, const void* in_base, size_t in_by
     return AES_OK;
 }
 
-// The whole opt-in shared memory; the attribute is set once per kernel and device.
+// The whole opt-in shared memory (the attribute is set once per kernel and context).
 static int batch_smem(BatchKernel fn, int* smem) {
     DeviceInfo info;
     int rc = current_device_info(&info);
     if (rc) return rc;
-    static std::mutex mu;
-    static std::set<std::pair<BatchKernel, int>> done;
-    std::lock_guard<std::mutex> lk(mu);
-    if (!done.count({fn, info.device})) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, info.smem_optin);
-        if (e != cudaSuccess) return fail(AES_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-        done.insert({fn, info.device});
-    }
+    rc = set_max_dynamic_smem((const void*)fn, info.smem_optin);
+    if (rc) return rc;
     *smem = info.smem_optin;
     return AES_OK;
 }
@@ -594,6 +588,13 @@ void aes_batch_plan_free(aes_batch_plan* P) {
 
 int aes_ecb_batch(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* ctxs, size_t nctx, const void* in_base,
                   size_t in_bytes, void* out_base, size_t out_bytes, void* stream) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(AES_ERR_STATE,
+                    "aes_ecb_batch uploads from host memory freed on return and cannot be captured; "
+                    "use aes_batch_plan_launch_graph");
     HostPlan H;
     int rc = build_host_plan(msgs, nmsg, ctxs, nctx, 2048, true, &H);
     if (rc) return rc;
@@ -611,7 +612,7 @@ int aes_ecb_batch(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* c
     memcpy(img.data() + off_msgs, H.msgs.data(), H.msgs.size() * sizeof(MsgDev));
     memcpy(img.data() + off_tiles, H.tile_msg.data(), H.tile_msg.size() * 4);
     uint8_t* buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&buf, bytes, s);
+    e = cudaMallocAsync((void**)&buf, bytes, s);
     if (e != cudaSuccess) return fail(AES_ERR_NOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
     e = cudaMemcpyAsync(buf, img.data(), bytes, cudaMemcpyHostToDevice, s);  // pageable: staged before return
     int* status = nullptr;
@@ -677,25 +678,29 @@ constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;  // 8 MiB
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
 static std::mutex g_noalloc_mu;
-static uint8_t* g_noalloc_addr[64];  // device address of g_noalloc_scratch, per device
+static std::vector<std::pair<unsigned long long, uint8_t*>> g_noalloc_addr;  // (context id, device address)
 
-// Device address of the scratch array on the current device.  Host code must
+// Device address of g_noalloc_scratch in the current context.  Host code must
 // not pass the array's own name to a kernel: on the host that name denotes a
-// host-side stand-in, not device memory.  Looked up once per device.
+// host-side stand-in, not device memory.  The address belongs to the module
+// loaded in one CUDA context, so it is looked up (cudaGetSymbolAddress, with
+// that context current) on the first call in each context -- normally once per
+// device, in its primary context -- and cached under the context's id.
 static int noalloc_scratch(uint8_t** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(AES_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= 64) return fail(AES_ERR_CUDA, "device index %d out of range", dev);
+    unsigned long long ctx = 0;
+    int rc = current_context_id(&ctx);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(AES_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-        g_noalloc_addr[dev] = (uint8_t*)p;
-    }
-    *out = g_noalloc_addr[dev];
+    for (const auto& e : g_noalloc_addr)
+        if (e.first == ctx) {
+            *out = e.second;
+            return AES_OK;
+        }
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return fail(AES_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_noalloc_addr.emplace_back(ctx, (uint8_t*)p);
+    *out = (uint8_t*)p;
     return AES_OK;
 }
 

@@ -105,10 +105,6 @@ __global__ void __launch_bounds__(1024, 1) table_kernel(const EcbArgs a) {
 
 }  // namespace gbaes
 
-#include <mutex>
-#include <set>
-#include <utility>
-
 namespace gbaes {
 
 namespace {
@@ -155,19 +151,10 @@ int launch_table(const EcbArgs& a, int nr, Mode mode, int threads, int bpt, cuda
     if (rc) return rc;
     // Dynamic shared memory: the whole opt-in limit, so the 64 KiB-aligned
     // layout fits wherever the dynamic window starts (the kernel re-checks).
-    // The attribute is set once per kernel and device.
     const int smem = info.smem_optin;
+    rc = set_max_dynamic_smem((const void*)fn, smem);
+    if (rc) return rc;
     cudaError_t e = cudaSuccess;
-    {
-        static std::mutex mu;
-        static std::set<std::pair<KernelFn, int>> done;
-        std::lock_guard<std::mutex> lk(mu);
-        if (!done.count({fn, info.device})) {
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return fail(AES_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-            done.insert({fn, info.device});
-        }
-    }
     // Small inputs: no more threads than blocks to process (a whole warp at least).
     const uint64_t need_threads = ((a.nblocks + bpt - 1) / bpt + 31) / 32 * 32;
     if (need_threads < (uint64_t)threads) threads = (int)(need_threads < 64 ? 64 : need_threads);

@@ -51,6 +51,14 @@ struct DeviceInfo {
 // Cached properties of the current device.  Returns AES_OK or an error code.
 int current_device_info(DeviceInfo* info);
 
+// Process-unique id of the CUDA context current on this thread (the device's
+// primary context is made current first if none is).
+int current_context_id(unsigned long long* id);
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for kernel fn, once per
+// (kernel, context).
+int set_max_dynamic_smem(const void* fn, int bytes);
+
 // Checks that [p, p+bytes) is 16-byte aligned device-reachable memory.
 int check_device_range(const void* p, size_t bytes, const char* what);
 

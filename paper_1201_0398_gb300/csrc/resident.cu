@@ -338,16 +338,8 @@ int launch_resident(const ResArgs& a, int threads, int bpt, cudaStream_t stream)
     DeviceInfo info;
     int rc = current_device_info(&info);
     if (rc) return rc;
-    {
-        static std::mutex mu;
-        static std::set<std::pair<ResidentKernel, int>> done;
-        std::lock_guard<std::mutex> lk(mu);
-        if (!done.count({fn, info.device})) {
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, info.smem_optin);
-            if (e != cudaSuccess) return fail(AES_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-            done.insert({fn, info.device});
-        }
-    }
+    rc = set_max_dynamic_smem((const void*)fn, info.smem_optin);
+    if (rc) return rc;
     fn<<<info.sms, threads, info.smem_optin, stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(AES_ERR_CUDA, "resident kernel launch: %s", cudaGetErrorString(e));

@@ -190,3 +190,23 @@ def test_batch_full_workload_10k_messages(gbaes, shape):
         got = host(y[a:a + take])
         assert np.array_equal(got, oracle.ecb(w.keys[i], int(w.bits[i]), src, decrypt=bool(w.decrypt[i])))
     assert gbaes.device_status() == 0
+
+
+@pytest.mark.gpu
+def test_one_shot_batch_refuses_stream_capture(gbaes):
+    """aes_ecb_batch uploads its tables from a host copy that is freed when the
+    call returns, so it refuses a stream that is being captured into a graph
+    (plans have their own graph path)."""
+    ks = [gbaes.Key(bytes(16))]
+    d = gbaes.make_descs([0], [0], [4], [0], [0])
+    x = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    y = torch.zeros_like(x)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        with pytest.raises(gbaes.AesError) as e:
+            gbaes.ecb_batch(d, ks, x, y)
+        y.add_(1)  # the graph captures this alone
+    assert e.value.name == "AES_ERR_STATE"
+    assert int(y.sum()) == 0  # captured, not run

@@ -1,4 +1,4 @@
-"""The usage shown in README.md, run as written on small data (GPU)."""
+"""The usage example of the package overview, run as written on small data (GPU)."""
 import numpy as np
 import pytest
 
