@@ -79,9 +79,18 @@ def parse_args():
     p.add_argument("--sweep", action="store_true",
                    help="size sweep 4 KiB - 16 GiB (powers of 4), AES-128/256 encrypt, table vs bitsliced kernel")
     p.add_argument("--sweep-max-gib", type=int, default=16)
+    p.add_argument("--no-cpu-sweep", action="store_true", help="--sweep: skip the CPU rows")
     p.add_argument("--serve-sweep", action="store_true",
                    help="serving latency against offered load (both server modes), one JSON line per point")
     p.add_argument("--serve-sweep-seconds", type=float, default=2.0)
+    p.add_argument("--serve-sweep-rates", default="200000,400000,800000,1600000,2400000",
+                   help="--serve-sweep: offered request rates (requests/s), comma separated")
+    p.add_argument("--serve-sweep-modes", default="resident,launch",
+                   help="--serve-sweep: server modes to run (resident, launch)")
+    p.add_argument("--serve-pin", action="store_true",
+                   help="--serve-sweep: pin the server's scheduler and replay threads to their own CPUs")
+    p.add_argument("--serve-sweep-shape", default="",
+                   help="--serve-sweep: resident tile shape THREADSxBLOCKS_PER_THREAD (default 512x2)")
     p.add_argument("--profile-case", choices=PROFILE_CASES,
                    help="run one small fixed case for an ncu capture (no timing, no JSON line)")
     p.add_argument("--profile-warmup", type=int, default=2)
@@ -588,7 +597,9 @@ def bench_batched(g, args, stream, ranks):
 
 def run_sweep(args):
     """One JSON line per (key size, kernel, buffer size): device-resident
-    uniform random bytes, CUDA-event time per launch (median of reps)."""
+    uniform random bytes; "ms" = CUDA-event time of reps back-to-back calls /
+    reps, "graph_us" (up to 16 MiB) = device time per call replayed from a
+    CUDA graph."""
     import torch
 
     import paper_1201_0398_gb300 as g
@@ -602,28 +613,62 @@ def run_sweep(args):
     sizes = [4096 * 4 ** i for i in range(12) if 4096 * 4 ** i <= args.sweep_max_gib * GiB]
     x = workloads.device_bytes(31, sizes[-1])
     y = torch.empty_like(x)
+    kernels = (("table", g.KERNEL_TABLE), ("table_compact", g.KERNEL_TABLE_COMPACT),
+               ("table_replicated", g.KERNEL_TABLE_REPLICATED), ("bitsliced", g.KERNEL_BITSLICED))
     for bits in (128, 256):
         k = g.Key(workloads.random_key(40 + bits, bits))
-        for kname, kid in (("table", g.KERNEL_TABLE), ("bitsliced", g.KERNEL_BITSLICED)):
+        for kname, kid in kernels:
             for size in sizes:
+                if kid == g.KERNEL_TABLE_COMPACT and size > 256 * MiB:
+                    continue
                 xs, ys = x[:size], y[:size]
                 reps = max(5, min(200, int(2 * GiB // size)))
                 for _ in range(3):
                     g.ecb_ex(k, xs, ys, kernel=kid, stream=stream)
-                times = []
-                for _ in range(reps):
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    g.ecb_ex(k, xs, ys, kernel=kid, stream=stream)
-                    e1.record(stream)
-                    times.append((e0, e1))
                 torch.cuda.synchronize()
-                ms = statistics.median(a.elapsed_time(b) for a, b in times)
+                # Back-to-back calls between two events: per call, the larger of
+                # the device time and the host's issue time (a small call from
+                # Python is host bound; graph_us below takes the host out).
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    g.ecb_ex(k, xs, ys, kernel=kid, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
                 gbs = size / (ms / 1e3) / 1e9
                 r_smem = sms * LOOKUPS_PER_CLK_PER_SM * f_max / NR[bits] / 1e9
-                print(json.dumps({"sweep": "aes-ecb-encrypt", "bits": bits, "kernel": kname, "bytes": size,
-                                  "ms": ms, "gbs": gbs, "reps": reps, "frac_smem_roofline": gbs / r_smem,
-                                  "hbm_frac": 2 * gbs / float(peaks["hbm_gbs"])}), flush=True)
+                line = {"sweep": "aes-ecb-encrypt", "bits": bits, "kernel": kname, "bytes": size, "ms": ms,
+                        "gbs": gbs, "reps": reps, "frac_smem_roofline": gbs / r_smem,
+                        "hbm_frac": 2 * gbs / float(peaks["hbm_gbs"])}
+                if size <= 16 * MiB:
+                    line["graph_us"] = graph_launch_us(torch, g, k, xs, ys, kid)
+                    line["graph_gbs"] = size / line["graph_us"] / 1e3
+                print(json.dumps(line), flush=True)
+
+
+def graph_launch_us(torch, g, k, xs, ys, kid, n=50, reps=5):
+    """Device time per call with the host out of the way: n calls of the C ABI
+    captured into one CUDA graph, the graph replayed, CUDA events around the
+    replay (median of reps replays) / n."""
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+        for _ in range(n):
+            g.ecb_ex(k, xs, ys, kernel=kid)
+    replay = torch.cuda.current_stream()  # CUDAGraph.replay launches on the current stream
+    graph.replay()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(replay)
+        graph.replay()
+        e1.record(replay)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e3 / n)
+    del graph
+    return statistics.median(ts)
 
 
 class OpenSSLECB:
@@ -732,13 +777,17 @@ def run_serve_sweep(args):
     from paper_1201_0398_gb300 import load, serving
 
     load()
-    for rate in (200_000.0, 400_000.0, 800_000.0, 1_600_000.0, 2_400_000.0):
-        for resident in (True, False):
-            r = serving.run(rate=rate, duration_s=args.serve_sweep_seconds, check_last=200, resident=resident)
+    modes = [m.strip() for m in args.serve_sweep_modes.split(",")]
+    threads, bpt = (int(v) for v in args.serve_sweep_shape.split("x")) if args.serve_sweep_shape else (0, 0)
+    for rate in (float(r) for r in args.serve_sweep_rates.split(",")):
+        for resident in (m == "resident" for m in modes):
+            shape = dict(threads=threads, blocks_per_thread=bpt) if resident else {}
+            r = serving.run(rate=rate, duration_s=args.serve_sweep_seconds, check_last=200, resident=resident,
+                            pin_threads=args.serve_pin, **shape)
             torch.cuda.empty_cache()
             keep = ("mode", "value", "offered_gbs", "requests", "completed_ok", "p50_ms", "p99_ms", "p999_ms",
                     "max_ms", "p50_queue_ms", "p50_service_ms", "max_queue", "max_inflight_bytes", "shape",
-                    "mismatches", "mean_batch_msgs")
+                    "mismatches", "mean_batch_msgs", "p50_service_ms", "p99_service_ms", "host_threads")
             print(json.dumps({"sweep": "serving", "rate": rate, "seconds": args.serve_sweep_seconds,
                               **{k: r[k] for k in keep if k in r}}), flush=True)
 
@@ -757,7 +806,8 @@ def run_profile_case(args):
                  for single-pass DRAM-byte captures at the bench size only
       bitsliced  64 MiB, AES-128 encryption + decryption, bitsliced kernel
       batch      10,000 messages, 16 B - 1 MiB (~0.95 GB), one batched launch each
-      sweep      one AES-128 encryption per size, 4 KiB - 1 GiB, table then bitsliced
+      sweep      one AES-128 encryption per size, 4 KiB - 1 GiB: table (size-dispatched),
+                 compact tables (up to 64 MiB), replicated tables, bitsliced
       singles    the 10,000-message batch as one batched launch, then as 10,000
                  single-message launches
     """
@@ -784,9 +834,10 @@ def run_profile_case(args):
         x = workloads.device_bytes(31, GiB)
         y = torch.empty_like(x)
         k = g.Key(workloads.random_key(168, 128))
-        for kid in (g.KERNEL_TABLE, g.KERNEL_BITSLICED):
+        for kid in (g.KERNEL_TABLE, g.KERNEL_TABLE_COMPACT, g.KERNEL_TABLE_REPLICATED, g.KERNEL_BITSLICED):
             for size in (4096 * 4 ** i for i in range(10)):  # 4 KiB .. 1 GiB
-                g.ecb_ex(k, x[:size], y[:size], kernel=kid)
+                if kid != g.KERNEL_TABLE_COMPACT or size <= 64 * MiB:
+                    g.ecb_ex(k, x[:size], y[:size], kernel=kid)
     else:
         w = workloads.batch_workload(n=10000, max_len=MiB) if case == "batch" else workloads.batch_workload()
         ks = [g.Key(k) for k in w.keys]
@@ -817,7 +868,8 @@ def main():
         return
     if args.sweep:
         run_sweep(args)
-        run_cpu_sweep()
+        if not args.no_cpu_sweep:
+            run_cpu_sweep()
         return
     if args.impl == "reference":
         run_reference(args)

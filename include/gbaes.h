@@ -54,8 +54,15 @@ extern "C" {
 #define AES_ERR_STATE (-8)   /* object used in the wrong state (e.g. closed server) */
 
 /* Kernel variants for aes_ecb_ex / aes_set_kernel. */
-#define AES_KERNEL_TABLE 0     /* Eq. 1 T-table kernel, tables in shared memory */
+#define AES_KERNEL_TABLE 0     /* Eq. 1 T-table kernel, tables in shared memory: the replicated
+                                  tables, or the compact ones for calls too small to fill the GPU */
 #define AES_KERNEL_BITSLICED 1 /* Boolean-circuit S-box over bit planes of 32 blocks */
+#define AES_KERNEL_TABLE_COMPACT 2    /* T-table kernel with each table stored once (4-5 KiB of shared
+                                         memory, cheap to fill; lookups may meet bank conflicts), any
+                                         size; its launch shape is its own (threads and
+                                         blocks_per_thread are ignored) */
+#define AES_KERNEL_TABLE_REPLICATED 3 /* T-table kernel with 32 lane copies of each table (bank-conflict
+                                         free, 128-160 KiB to fill per CTA), any size */
 
 /* Counter layouts for aes_ctr_xcrypt (Section 3, CTR mode). */
 #define AES_CTR_BE128 0     /* IV is one big-endian 128-bit integer (NIST SP 800-38A) */
@@ -239,9 +246,11 @@ void aes_pipeline_free(aes_pipeline* pipe);
  * admitted.  The scheduler cuts each request into tiles of at most threads *
  * blocks_per_thread blocks (spread over the idle CTAs, at least 256 blocks
  * each), writes them into a ring in mapped page-locked memory and publishes
- * them with a release store; CTAs take tiles with tickets from an atomic
- * counter, and the CTA that finishes a request's last tile appends it to a
- * completion queue in page-locked memory, which the scheduler reads.  No
+ * them with a release store; in each CTA a producer warp takes tiles with
+ * tickets from an atomic counter and stages the next tile's record while the
+ * compute threads encipher the current one, and a completer warp counts
+ * finished tiles and appends each finished request to a completion queue in
+ * page-locked memory, which the scheduler reads.  No
  * launch, copy or event per request.  The scheduler stops the kernel after
  * resident_idle_us without work and before resident_lifetime_ms (its bound on
  * the GPU) have passed, and relaunches it when work arrives.  While it runs it
@@ -252,13 +261,19 @@ void aes_pipeline_free(aes_pipeline* pipe);
  * Stats: `batches` counts kernel launches, batch_msgs is 1. */
 #define AES_SERVER_RESIDENT 2
 
+/* Pins the scheduler thread to the last CPU of the process's affinity set and
+ * the replay thread to the one before it (pthread_setaffinity_np), so that
+ * neither migrates; other threads of the process may still share those CPUs. */
+#define AES_SERVER_PIN_THREADS 4
+
 typedef struct aes_server aes_server;
 
 typedef struct aes_server_config {
     uint64_t budget_bytes;      /* in+out bytes in flight (0 = 8 GiB) */
     int32_t nstreams;           /* stream slots, 1..64 (0 = 4) */
     int32_t flags;              /* AES_SERVER_* */
-    int32_t threads;            /* batched-kernel (or resident-kernel) CTA size (0 = 512) */
+    int32_t threads;            /* batched-kernel CTA size, or the resident kernel's compute threads per CTA
+                                   (at most 512; two control warps come on top) (0 = 512) */
     int32_t blocks_per_thread;  /* 1, 2 or 4 (0 = 1; resident mode: 2) */
     uint32_t max_batch_msgs;    /* requests per batch (0 = 4096) */
     uint32_t dryrun_batch_us;   /* AES_SERVER_DRYRUN only: simulated time a batch spends "on the GPU" */
@@ -299,6 +314,21 @@ typedef struct aes_server_stats {
     uint64_t max_batch_msgs;
     uint64_t budget_bytes;
     uint64_t recovered_tiles;    /* resident mode: tiles re-published after the kernel's own bound ended it */
+    /* Host-thread diagnostics, for latency tails: the scheduler thread, then the
+     * replay thread.  The scheduler reads its own CPU time and context-switch
+     * counts (getrusage) every 16 passes and after any pass that comes more than
+     * 50 us after the one before; between two readings lies a window. */
+    uint64_t sched_passes;              /* scheduler passes */
+    uint64_t sched_worst_window_ns;     /* longest window in which the scheduler had work waiting throughout */
+    uint64_t sched_worst_window_cpu_ns; /* CPU time the scheduler got in that window */
+    uint64_t sched_worst_window_invol;  /* involuntary context switches (preemptions) in that window */
+    uint64_t sched_invol;               /* involuntary context switches of the scheduler over the server's life */
+    uint64_t sched_lock_wait_max_ns;    /* the scheduler's longest wait for a lock other threads share */
+    uint64_t producer_late_max_ns;      /* replay: latest hand-over of requests after the first one's arrival time */
+    uint64_t producer_late_invol;       /* replay: involuntary switches since the reading before that hand-over */
+    uint64_t producer_invol;            /* replay: involuntary context switches over all replays */
+    int64_t sched_cpu;                  /* CPU the scheduler thread is pinned to (AES_SERVER_PIN_THREADS), else -1 */
+    int64_t producer_cpu;               /* CPU the replay thread is pinned to, else -1 */
 } aes_server_stats;
 
 /* Creates a server on the current device with nkeys resident key contexts

@@ -40,6 +40,7 @@ __all__ = [
     "Server",
     "SERVER_DRYRUN",
     "SERVER_RESIDENT",
+    "SERVER_PIN_THREADS",
     "Router",
     "ROUTE_LEAST_LOADED",
     "ROUTE_BY_DEVICE",
@@ -47,12 +48,16 @@ __all__ = [
     "COMPLETION",
     "KERNEL_TABLE",
     "KERNEL_BITSLICED",
+    "KERNEL_TABLE_COMPACT",
+    "KERNEL_TABLE_REPLICATED",
     "CTR_BE128",
     "CTR_LE32_CARRY",
 ]
 
 KERNEL_TABLE = 0
 KERNEL_BITSLICED = 1
+KERNEL_TABLE_COMPACT = 2
+KERNEL_TABLE_REPLICATED = 3
 CTR_BE128 = 0
 CTR_LE32_CARRY = 1
 
@@ -162,10 +167,26 @@ def _u8p(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
 
 
-def _stream_handle(stream):
-    import torch
+_torch = None
 
+
+def _torch_mod():
+    global _torch
+    if _torch is None:
+        import torch
+
+        _torch = torch
+    return _torch
+
+
+def _stream_handle(stream):
+    torch = _torch_mod()
     if stream is None:
+        # The current stream's raw handle without building a Stream object
+        # (that costs microseconds per call, as much as the launch itself).
+        raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        if raw is not None:
+            return ctypes.c_void_p(raw(torch.cuda.current_device()))
         stream = torch.cuda.current_stream()
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
@@ -180,8 +201,7 @@ def _nblocks(t) -> int:
 
 
 def _ptr(t):
-    import torch
-
+    torch = _torch_mod()
     if not isinstance(t, torch.Tensor):
         raise TypeError("expected a torch.Tensor")
     if not t.is_contiguous():
@@ -218,8 +238,7 @@ class Key:
 
 
 def _out_like(x, out):
-    import torch
-
+    torch = _torch_mod()
     if out is None:
         out = torch.empty_like(x)
     if out.numel() * out.element_size() != x.numel() * x.element_size():
@@ -425,6 +444,7 @@ class Pipeline:
 
 SERVER_DRYRUN = 1
 SERVER_RESIDENT = 2
+SERVER_PIN_THREADS = 4
 
 # Match aes_server_request / aes_server_completion (48 and 40 bytes).
 REQUEST = np.dtype([("id", "<u8"), ("in_ptr", "<u8"), ("out_ptr", "<u8"), ("nblocks", "<u8"), ("key_index", "<u4"),
@@ -445,7 +465,11 @@ class _ServerConfig(ctypes.Structure):
 class _ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "rejected", "batches",
                                                "max_inflight_bytes", "max_queue", "max_batch_msgs", "budget_bytes",
-                                               "recovered_tiles")]
+                                               "recovered_tiles", "sched_passes", "sched_worst_window_ns",
+                                               "sched_worst_window_cpu_ns", "sched_worst_window_invol", "sched_invol",
+                                               "sched_lock_wait_max_ns", "producer_late_max_ns",
+                                               "producer_late_invol", "producer_invol")] + [
+        ("sched_cpu", ctypes.c_int64), ("producer_cpu", ctypes.c_int64)]
 
 
 class Server:
@@ -457,10 +481,11 @@ class Server:
                  blocks_per_thread: int = 0, max_batch_msgs: int = 0, max_batch_blocks: int = 0, dryrun: bool = False,
                  dryrun_batch_us: int = 0, resident: bool = False, resident_idle_us: int = 0,
                  resident_lifetime_ms: int = 0, ring_tiles: int = 0, ring_items: int = 0,
-                 resident_restart_pct: int = 0):
+                 resident_restart_pct: int = 0, pin_threads: bool = False):
         self._lib = load()
         self._keys = list(keys)
-        flags = (SERVER_DRYRUN if dryrun else 0) | (SERVER_RESIDENT if resident else 0)
+        flags = ((SERVER_DRYRUN if dryrun else 0) | (SERVER_RESIDENT if resident else 0) |
+                 (SERVER_PIN_THREADS if pin_threads else 0))
         cfg = _ServerConfig(int(budget_bytes), int(nstreams), flags, int(threads), int(blocks_per_thread),
                             int(max_batch_msgs), int(dryrun_batch_us), int(max_batch_blocks), int(resident_idle_us),
                             int(resident_lifetime_ms), int(ring_tiles), int(ring_items), int(resident_restart_pct))

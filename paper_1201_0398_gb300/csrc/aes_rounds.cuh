@@ -75,17 +75,16 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t v) {
     asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(addr), "r"(v));
 }
 
-// Writes the tables of one direction into shared memory at A (all threads of
-// the CTA take part; the caller synchronises afterwards).  Pair p = (entry x =
-// p/4, table k = p%4): its 32 lane copies are 128 contiguous bytes at region
-// k/2, slot k%2, written as eight 16-byte stores in an order rotated by p, so
-// the 8 threads of each quarter-warp hit 8 different bank groups.  A thread
-// loads the entries of up to four pairs before storing any, so small CTAs
-// (many pairs per thread) overlap the global loads.
-__device__ __forceinline__ void fill_tables(uint32_t A, bool decrypt) {
+// Writes the tables of one direction into shared memory at A; threads tid =
+// 0..nt-1 take part (fill_tables: the whole CTA), and the caller synchronises
+// them afterwards.  Pair p = (entry x = p/4, table k = p%4): its 32 lane copies
+// are 128 contiguous bytes at region k/2, slot k%2, written as eight 16-byte
+// stores in an order rotated by p, so the 8 threads of each quarter-warp hit 8
+// different bank groups.  A thread loads the entries of up to four pairs before
+// storing any, so small CTAs (many pairs per thread) overlap the global loads.
+__device__ __forceinline__ void fill_tables_n(uint32_t A, bool decrypt, uint32_t tid, uint32_t nt) {
     const uint32_t* t0 = decrypt ? g_tab.td0 : g_tab.te0;
-    const uint32_t nt = blockDim.x;
-    for (uint32_t p0 = threadIdx.x; p0 < 1024u; p0 += 4u * nt) {
+    for (uint32_t p0 = tid; p0 < 1024u; p0 += 4u * nt) {
         uint32_t v[4];
 #pragma unroll
         for (uint32_t u = 0; u < 4; ++u) {
@@ -105,7 +104,7 @@ __device__ __forceinline__ void fill_tables(uint32_t A, bool decrypt) {
         }
     }
     if (decrypt) {
-        for (uint32_t x0 = threadIdx.x; x0 < 256u; x0 += 4u * nt) {
+        for (uint32_t x0 = tid; x0 < 256u; x0 += 4u * nt) {
             uint32_t v[4];
 #pragma unroll
             for (uint32_t u = 0; u < 4; ++u) {
@@ -124,6 +123,8 @@ __device__ __forceinline__ void fill_tables(uint32_t A, bool decrypt) {
         }
     }
 }
+
+__device__ __forceinline__ void fill_tables(uint32_t A, bool decrypt) { fill_tables_n(A, decrypt, threadIdx.x, blockDim.x); }
 
 // Address of T_{2*region+slot}[byte K of w] for this lane (region offset aside):
 // byte 0 <- lane constant (l<<2 | slot<<7), byte 1 <- byte K of w, bytes 2,3 <-
@@ -220,12 +221,6 @@ struct ParamKeys {
     __device__ __forceinline__ uint4 get(int r) const {
         return make_uint4(rk[4 * r], rk[4 * r + 1], rk[4 * r + 2], rk[4 * r + 3]);
     }
-};
-
-// Round keys from a schedule in global memory (read-only path; 16 B per round).
-struct GlobalKeys {
-    const uint4* p;
-    __device__ __forceinline__ uint4 get(int r) const { return __ldg(p + r); }
 };
 
 // Full cipher on BPT independent states sharing one schedule, rounds

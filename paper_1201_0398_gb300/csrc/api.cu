@@ -245,6 +245,10 @@ int table_default_shape(int bits, int decrypt, int* threads, int* bpt) {
 
 static bool valid_threads(int t) { return t >= 64 && t <= 1024 && t % 32 == 0; }
 static bool valid_bpt(int b) { return b == 1 || b == 2 || b == 4; }
+static bool valid_kernel(int k) {
+    return k == AES_KERNEL_TABLE || k == AES_KERNEL_BITSLICED || k == AES_KERNEL_TABLE_COMPACT ||
+           k == AES_KERNEL_TABLE_REPLICATED;
+}
 
 static int check_ctx(const aes_ctx* ctx) {
     if (!ctx || ctx->magic != kCtxMagic) return fail(AES_ERR_ARG, "invalid or freed aes_ctx");
@@ -305,7 +309,7 @@ static int run_block_op(const aes_ctx* ctx, Mode mode, const void* in, void* out
         if (mode != kEnc && mode != kDec) return fail(AES_ERR_ARG, "the bitsliced kernel implements ECB only");
         return launch_bitsliced(a, ctx->enc_rk, ctx->nr, mode, threads, (cudaStream_t)stream);
     }
-    return launch_table(a, ctx->nr, mode, threads, bpt, (cudaStream_t)stream);
+    return launch_table(a, ctx->nr, mode, threads, bpt, kernel, (cudaStream_t)stream);
 }
 
 }  // namespace gbaes
@@ -358,12 +362,12 @@ int aes_ecb_ex(const aes_ctx* ctx, int decrypt, const void* in, void* out, size_
                int blocks_per_thread, void* stream) {
     if (check_ctx(ctx)) return AES_ERR_ARG;
     if (decrypt != 0 && decrypt != 1) return fail(AES_ERR_ARG, "decrypt must be 0 or 1");
-    if (kernel != AES_KERNEL_TABLE && kernel != AES_KERNEL_BITSLICED) return fail(AES_ERR_ARG, "unknown kernel %d", kernel);
+    if (!valid_kernel(kernel)) return fail(AES_ERR_ARG, "unknown kernel %d", kernel);
     Tuning t = get_tuning(ctx->bits, decrypt);
     if (threads == 0) threads = kernel == AES_KERNEL_BITSLICED ? 256 : t.threads;
     if (blocks_per_thread == 0) blocks_per_thread = t.bpt;
     if (!valid_threads(threads)) return fail(AES_ERR_ARG, "threads %d: need a multiple of 32 in [64, 1024]", threads);
-    if (kernel == AES_KERNEL_TABLE && !valid_bpt(blocks_per_thread))
+    if (kernel != AES_KERNEL_BITSLICED && !valid_bpt(blocks_per_thread))
         return fail(AES_ERR_ARG, "blocks_per_thread %d: need 1, 2 or 4", blocks_per_thread);
     return run_block_op(ctx, decrypt ? kDec : kEnc, in, out, nblocks, kernel, threads, blocks_per_thread, stream,
                         nullptr, 0, 0);
@@ -390,7 +394,7 @@ int aes_cbc_decrypt(const aes_ctx* ctx, const uint8_t* iv, const void* in, void*
 }
 
 int aes_set_kernel(int which) {
-    if (which != AES_KERNEL_TABLE && which != AES_KERNEL_BITSLICED) return fail(AES_ERR_ARG, "unknown kernel %d", which);
+    if (!valid_kernel(which)) return fail(AES_ERR_ARG, "unknown kernel %d", which);
     return g_kernel.exchange(which);
 }
 

@@ -88,7 +88,10 @@ __device__ __forceinline__ void single_message_tile(const BatchArgs& a, const Gr
 
 // A tile that crosses message boundaries (messages m_lo..m_hi, m_lo < m_hi):
 // each block finds its message by binary search over that range and reads its
-// round keys from global memory through L1.
+// round keys from global memory through L1.  The states of one thread may
+// belong to different messages: each carries its own key pointer, so the
+// warp runs one interleaved cipher over all of them (no divergent per-block
+// ciphers at a message boundary).
 template <bool DEC, int BPT>
 __device__ __forceinline__ void mixed_tile(const BatchArgs& a, const GroupDev& G, uint32_t m_lo, uint32_t m_hi,
                                            uint64_t tb0, uint32_t lane, uint32_t L0, uint32_t L1) {
@@ -130,18 +133,10 @@ __device__ __forceinline__ void mixed_tile(const BatchArgs& a, const GroupDev& G
             s[b][3] = v.w;
         }
         if (!ok[0]) return;  // blocks only increase: nothing left in this tile for this lane
-        bool same = true;
 #pragma unroll
-        for (int b = 1; b < BPT; ++b) same = same && (!ok[b] || kp[b] == kp[0]);
-        if (same) {
-            cipher_rt<DEC, BPT>(s, GlobalKeys{kp[0]}, G.nr, L0, L1);
-        } else {
-#pragma unroll
-            for (int b = 0; b < BPT; ++b) {
-                if (ok[b])
-                    cipher_rt<DEC, 1>(*reinterpret_cast<uint32_t(*)[1][4]>(&s[b]), GlobalKeys{kp[b]}, G.nr, L0, L1);
-            }
-        }
+        for (int b = 1; b < BPT; ++b)
+            if (!ok[b]) kp[b] = kp[0];  // (past the end: computes on zeros with a valid key, stores nothing)
+        cipher_rt<DEC, BPT>(s, StateKeys<BPT>{kp}, G.nr, L0, L1);
 #pragma unroll
         for (int b = 0; b < BPT; ++b)
             if (ok[b]) __stcs(a.out + oidx[b], make_uint4(s[b][0], s[b][1], s[b][2], s[b][3]));

@@ -62,8 +62,13 @@ int set_max_dynamic_smem(const void* fn, int bytes);
 // Checks that [p, p+bytes) is 16-byte aligned device-reachable memory.
 int check_device_range(const void* p, size_t bytes, const char* what);
 
-// Launches the T-table kernel (ecb_table.cu).
-int launch_table(const EcbArgs& a, int nr, Mode mode, int threads, int bpt, cudaStream_t stream);
+// Largest call (in blocks) that AES_KERNEL_TABLE runs with compact tables.
+uint64_t compact_limit_blocks(int sms);
+
+// Launches the T-table kernel (ecb_table.cu).  variant: AES_KERNEL_TABLE (picks
+// by size), AES_KERNEL_TABLE_COMPACT or AES_KERNEL_TABLE_REPLICATED; threads
+// and bpt shape the replicated kernel only.
+int launch_table(const EcbArgs& a, int nr, Mode mode, int threads, int bpt, int variant, cudaStream_t stream);
 
 // Launches the bitsliced kernel (ecb_bitsliced.cu), ECB only.
 int launch_bitsliced(const EcbArgs& a, const uint32_t* enc_rk, int nr, Mode mode, int threads, cudaStream_t stream);

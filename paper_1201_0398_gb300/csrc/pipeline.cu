@@ -132,7 +132,7 @@ int aes_pipeline_ecb(aes_pipeline* P, const aes_ctx* ctx, int decrypt, const voi
         a.in = (const uint4*)P->slot_buf[s];
         a.out = (uint4*)P->slot_buf[s];
         a.nblocks = n / 16;
-        rc = launch_table(a, ctx->nr, mode, threads, bpt, st);
+        rc = launch_table(a, ctx->nr, mode, threads, bpt, AES_KERNEL_TABLE, st);
         if (rc) return rc;
         e = cudaMemcpyAsync((uint8_t*)host_out + off, P->slot_buf[s], n, cudaMemcpyDefault, st);
         if (e != cudaSuccess) return fail(AES_ERR_CUDA, "copy out: %s", cudaGetErrorString(e));

@@ -42,12 +42,25 @@ static_assert(sizeof(ResCtrl) == 64, "one cache line");
 
 constexpr uint32_t kAbandonCap = 1024;  // per direction (a CTA holds at most one ticket per direction)
 
-// One completion: entry i of the completion queue holds tag = i + 1 (written
-// last, with a release store) and what = direction << 63 | request number.
+// One completion: the i-th completion goes to entry i % cq_size as one word,
+// written with a single release store:
+//   lap << 40 | direction << 39 | (request number mod 2^39),
+// where lap = (i / cq_size + 1) mod 2^24 tells the host a fresh entry from
+// the one the previous lap left there (the host knows which lap it expects).
+// At most cq_size requests are in flight, so an entry is always consumed
+// before the next lap overwrites it, and 2^39 requests in flight can tell
+// every request number from its low bits.
 struct ResDone {
-    uint64_t tag;
-    uint64_t what;
+    uint64_t word;
 };
+
+constexpr uint64_t kCqSeqMask = (1ull << 39) - 1;
+
+__host__ __device__ inline uint64_t cq_lap(uint64_t i, uint32_t cq_log2) { return ((i >> cq_log2) + 1) & 0xFFFFFFull; }
+
+__host__ __device__ inline uint64_t cq_word(uint64_t i, uint32_t cq_log2, int dir, uint64_t seq) {
+    return cq_lap(i, cq_log2) << 40 | (uint64_t)dir << 39 | (seq & kCqSeqMask);
+}
 
 struct ResArgs {
     const ResTile* tiles;           // [2][ring_tiles], device view of page-locked memory
@@ -63,11 +76,16 @@ struct ResArgs {
     uint32_t ring_tiles;            // power of two
     uint32_t ring_items;            // power of two
     uint32_t cq_size;               // power of two, 2 * ring_items (requests in flight, both directions)
+    uint32_t cq_log2;               // log2(cq_size)
     uint64_t lifetime_ns;           // a CTA leaves once this long has passed since its start
 };
 
-// Launches the resident kernel: one CTA per SM, `threads` threads each,
-// `bpt` (1, 2 or 4) blocks per thread per tile.
+// Compute threads per CTA of the resident kernel (at most; two control warps come on top).
+constexpr uint32_t kResidentMaxThreads = 512;
+
+// Launches the resident kernel: one CTA per SM, `threads` compute threads
+// (64..kResidentMaxThreads, a multiple of 32) plus two control warps each, `bpt`
+// (1, 2 or 4) blocks per compute thread per tile.
 int launch_resident(const ResArgs& a, int threads, int bpt, cudaStream_t stream);
 
 }  // namespace gbaes

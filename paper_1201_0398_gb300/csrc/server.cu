@@ -31,6 +31,9 @@
 // protocol), so the scheduling logic (admission, budget, batching, the ring,
 // cancellation, fault handling, drain) can be exercised without a GPU.
 #include <cuda_runtime.h>
+#include <pthread.h>
+#include <sched.h>
+#include <sys/resource.h>
 
 #include <algorithm>
 #include <atomic>
@@ -76,6 +79,60 @@ struct ResItem {
     uint64_t bytes;       // in+out bytes charged to the budget
     double launch_s;      // when it was published
     bool done;
+};
+
+// Scheduling diagnostics of one host thread, kept by that thread.  Every 16th
+// pass, and on a pass that comes more than 50 us after the one before, it
+// reads the thread's own CPU time and context-switch counts
+// (getrusage(RUSAGE_THREAD)), closing a window.  The longest window in which
+// the thread had work waiting throughout (it never slept on purpose) is kept
+// with the CPU time the thread got in it and the involuntary switches
+// (preemptions) it suffered: a window whose wall time far exceeds its CPU
+// time, with involuntary switches, is time the thread was descheduled.
+struct ThreadWatch {
+    double win_start = 0, cpu_start = 0, prev_pass = 0;
+    long invol_start = 0;
+    bool win_busy = true, started = false;
+    uint32_t passes = 0;
+    uint64_t npasses = 0;
+    double worst_wall = 0, worst_cpu = 0;
+    long worst_invol = 0, invol_total = 0;
+
+    static void usage(double* cpu, long* invol) {
+        struct rusage u;
+        memset(&u, 0, sizeof u);
+        getrusage(RUSAGE_THREAD, &u);
+        *cpu = (double)u.ru_utime.tv_sec + 1e-6 * u.ru_utime.tv_usec + (double)u.ru_stime.tv_sec +
+               1e-6 * u.ru_stime.tv_usec;
+        *invol = u.ru_nivcsw;
+    }
+    void sample(double now) {
+        double cpu;
+        long invol;
+        usage(&cpu, &invol);
+        if (started) {
+            invol_total += invol - invol_start;
+            if (win_busy && now - win_start > worst_wall) {
+                worst_wall = now - win_start;
+                worst_cpu = cpu - cpu_start;
+                worst_invol = invol - invol_start;
+            }
+        }
+        started = true;
+        win_start = now;
+        cpu_start = cpu;
+        invol_start = invol;
+        win_busy = true;
+    }
+    // A pass at `now`; busy: the thread had work waiting since its previous pass.
+    void pass(double now, bool busy) {
+        if (!started) sample(now);
+        win_busy = win_busy && busy;
+        const bool late = now - prev_pass > 50e-6;
+        prev_pass = now;
+        ++npasses;
+        if (++passes % 16 == 0 || late) sample(now);
+    }
 };
 
 }  // namespace gbaes
@@ -152,12 +209,70 @@ struct aes_server {
     std::thread fake;
     std::atomic<bool> fake_running{false};
 
+    // Host-thread diagnostics (aes_server_stats): the scheduler's, kept by the
+    // scheduler thread; the replay thread's, kept by that thread.
+    ThreadWatch sched_watch;
+    double lock_wait_max = 0;     // scheduler: longest wait for a lock shared with other threads
+    double late_max = 0;          // replay: latest hand-over after a request's scheduled arrival
+    long late_invol = 0;          // replay: involuntary switches in the window of that hand-over
+    long producer_invol = 0;      // replay: involuntary switches over the replays
+    int sched_cpu = -1, producer_cpu = -1;  // CPU each thread is pinned to (AES_SERVER_PIN_THREADS), or -1
+    bool sched_slept = false;     // scheduler: its last idle wait slept on the condition variable
+
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
 };
 
 namespace gbaes {
+
+// A lock taken by the scheduler thread on a mutex that other threads share;
+// the wait counts toward the scheduler's longest lock wait.
+class SchedLock {
+   public:
+    SchedLock(aes_server* S, std::mutex& m) : m_(m) {
+        const auto t = std::chrono::steady_clock::now();
+        m_.lock();
+        const double w = std::chrono::duration<double>(std::chrono::steady_clock::now() - t).count();
+        if (w > S->lock_wait_max) S->lock_wait_max = w;
+    }
+    ~SchedLock() { m_.unlock(); }
+    SchedLock(const SchedLock&) = delete;
+    SchedLock& operator=(const SchedLock&) = delete;
+
+   private:
+    std::mutex& m_;
+};
+
+// Pins the calling thread to one CPU of the process's affinity set: the
+// last (which = 0) or the one before it (which = 1).  Returns the CPU or -1.
+static int pin_thread(int which) {
+    cpu_set_t set;
+    CPU_ZERO(&set);
+    if (sched_getaffinity(0, sizeof set, &set) != 0) return -1;
+    int found = 0;
+    for (int c = CPU_SETSIZE - 1; c >= 0; --c) {
+        if (!CPU_ISSET(c, &set)) continue;
+        if (found++ < which) continue;
+        cpu_set_t one;
+        CPU_ZERO(&one);
+        CPU_SET(c, &one);
+        return pthread_setaffinity_np(pthread_self(), sizeof one, &one) == 0 ? c : -1;
+    }
+    return -1;
+}
+
+// Copies the scheduler's diagnostics into the stats (caller holds stats_mu).
+static void publish_diagnostics(aes_server* S) {
+    const ThreadWatch& w = S->sched_watch;
+    S->stats.sched_passes = w.npasses;
+    S->stats.sched_worst_window_ns = (uint64_t)(1e9 * w.worst_wall);
+    S->stats.sched_worst_window_cpu_ns = (uint64_t)(1e9 * w.worst_cpu);
+    S->stats.sched_worst_window_invol = (uint64_t)w.worst_invol;
+    S->stats.sched_invol = (uint64_t)w.invol_total;
+    S->stats.sched_lock_wait_max_ns = (uint64_t)(1e9 * S->lock_wait_max);
+    S->stats.sched_cpu = S->sched_cpu;
+}
 
 static void complete(aes_server* S, std::vector<Pending>& reqs, int status, double launch_s, double done_s) {
     std::vector<aes_server_completion> out;
@@ -173,11 +288,11 @@ static void complete(aes_server* S, std::vector<Pending>& reqs, int status, doub
         out.push_back(c);
     }
     {
-        std::lock_guard<std::mutex> lk(S->out_mu);
+        SchedLock lk(S, S->out_mu);
         S->done.insert(S->done.end(), out.begin(), out.end());
     }
     {
-        std::lock_guard<std::mutex> lk(S->stats_mu);
+        SchedLock lk(S, S->stats_mu);
         S->stats.completed += reqs.size();
         if (status != AES_OK) S->stats.failed += reqs.size();
     }
@@ -243,7 +358,7 @@ static bool take_inbox(aes_server* S) {
     if (S->inbox_n.load(std::memory_order_acquire) == 0 && !S->cancels_n.load(std::memory_order_acquire))
         return false;  // nothing new: leave the lock to the producers
     {
-        std::lock_guard<std::mutex> lk(S->in_mu);
+        SchedLock lk(S, S->in_mu);
         if (!S->inbox.empty()) {
             for (Pending& p : S->inbox) S->queue.push_back(p);
             S->inbox.clear();
@@ -280,6 +395,7 @@ static bool idle_wait(aes_server* S, bool idle) {
         std::this_thread::yield();
         return true;
     }
+    S->sched_slept = true;  // (the scheduler's next pass closes no "busy" window)
     std::unique_lock<std::mutex> lk(S->in_mu);
     if (S->inbox.empty() && S->cancels.empty() && S->stop.load()) return false;
     S->in_cv.wait_for(lk, std::chrono::milliseconds(1),
@@ -289,7 +405,10 @@ static bool idle_wait(aes_server* S, bool idle) {
 
 static void scheduler_main(aes_server* S) {
     if (!S->dryrun) cudaSetDevice(S->device);
+    if (S->cfg.flags & AES_SERVER_PIN_THREADS) S->sched_cpu = pin_thread(0);
     for (;;) {
+        S->sched_watch.pass(S->now(), !S->sched_slept);
+        S->sched_slept = false;
         bool worked = take_inbox(S);
         // Completions.
         for (Slot& slot : S->slots) {
@@ -328,7 +447,7 @@ static void scheduler_main(aes_server* S) {
             int rc = launch_slot(S, slot);
             if (rc != AES_OK && !S->dryrun) cudaStreamSynchronize(slot.stream);  // staging may still be read
             {
-                std::lock_guard<std::mutex> lk(S->stats_mu);
+                SchedLock lk(S, S->stats_mu);
                 S->stats.batches++;
                 S->stats.max_batch_msgs = std::max<uint64_t>(S->stats.max_batch_msgs, slot.reqs.size());
             }
@@ -338,14 +457,15 @@ static void scheduler_main(aes_server* S) {
                 slot.busy = true;
                 slot.bytes = bytes;
                 S->inflight_bytes += bytes;
-                std::lock_guard<std::mutex> lk(S->stats_mu);
+                SchedLock lk(S, S->stats_mu);
                 S->stats.max_inflight_bytes = std::max<uint64_t>(S->stats.max_inflight_bytes, S->inflight_bytes);
             }
             worked = true;
         }
         {
-            std::lock_guard<std::mutex> lk(S->stats_mu);
+            SchedLock lk(S, S->stats_mu);
             S->stats.max_queue = std::max<uint64_t>(S->stats.max_queue, S->queue.size());
+            publish_diagnostics(S);
         }
         if (!worked) {
             bool idle = S->queue.empty();
@@ -430,9 +550,8 @@ static void fake_kernel_main(aes_server* S) {
         if (done == R.item_blocks) {
             done = 0;
             const uint64_t i = S->fake_cq_next++;
-            ResDone* e = &S->rcq[i & (S->rargs.cq_size - 1)];
-            __atomic_store_n(&e->what, ((uint64_t)got << 63) | R.seq, __ATOMIC_RELAXED);
-            __atomic_store_n(&e->tag, i + 1, __ATOMIC_RELEASE);
+            __atomic_store_n(&S->rcq[i & (S->rargs.cq_size - 1)].word, cq_word(i, S->rargs.cq_log2, got, R.seq),
+                             __ATOMIC_RELEASE);
         }
     }
     S->fake_running.store(false, std::memory_order_release);
@@ -602,6 +721,7 @@ static bool publish(aes_server* S, const Pending& p, uint64_t bytes, double now)
 
 static void scheduler_resident(aes_server* S) {
     if (!S->dryrun) cudaSetDevice(S->device);
+    if (S->cfg.flags & AES_SERVER_PIN_THREADS) S->sched_cpu = pin_thread(0);
     double last_work = S->now(), last_query = 0;
     std::vector<aes_server_completion> finished;
     const double idle_s = 1e-6 * S->cfg.resident_idle_us;
@@ -615,15 +735,18 @@ static void scheduler_resident(aes_server* S) {
         // have finished).
         finished.clear();
         const double pass_s = S->now();  // one clock read per pass, not per request
+        S->sched_watch.pass(pass_s, !S->sched_slept);
+        S->sched_slept = false;
         for (;;) {
             const ResDone* e = &S->rcq[S->rcq_head & (S->rargs.cq_size - 1)];
-            if (__atomic_load_n(&e->tag, __ATOMIC_ACQUIRE) != S->rcq_head + 1) break;
-            const uint64_t what = __atomic_load_n(&e->what, __ATOMIC_RELAXED);
+            const uint64_t w = __atomic_load_n(&e->word, __ATOMIC_ACQUIRE);
+            if ((w >> 40) != cq_lap(S->rcq_head, S->rargs.cq_log2)) break;  // not written in this lap yet
             ++S->rcq_head;
-            const int d = (int)(what >> 63);
-            const uint64_t seq = what & ~(1ull << 63);
+            const int d = (int)((w >> 39) & 1u);
             std::deque<ResItem>& q = S->rinflight[d];
-            if (q.empty() || seq < q.front().seq || seq - q.front().seq >= q.size()) continue;  // (not in flight)
+            if (q.empty()) continue;  // (not in flight)
+            const uint64_t seq = q.front().seq + (((w & kCqSeqMask) - q.front().seq) & kCqSeqMask);
+            if (seq - q.front().seq >= q.size()) continue;  // (not in flight)
             ResItem& it = q[seq - q.front().seq];
             if (it.done) continue;
             it.done = true;
@@ -641,11 +764,11 @@ static void scheduler_resident(aes_server* S) {
         }
         if (!finished.empty()) {  // one hand-over per pass, not one per request
             {
-                std::lock_guard<std::mutex> lk(S->out_mu);
+                SchedLock lk(S, S->out_mu);
                 S->done.insert(S->done.end(), finished.begin(), finished.end());
             }
             {
-                std::lock_guard<std::mutex> lk(S->stats_mu);
+                SchedLock lk(S, S->stats_mu);
                 S->stats.completed += finished.size();
             }
             S->finished.fetch_add(finished.size());
@@ -706,18 +829,19 @@ static void scheduler_resident(aes_server* S) {
             worked = true;
         }
         {
-            std::lock_guard<std::mutex> lk(S->stats_mu);
+            SchedLock lk(S, S->stats_mu);
             if (admitted) {
                 S->stats.max_inflight_bytes = std::max<uint64_t>(S->stats.max_inflight_bytes, S->inflight_bytes);
                 S->stats.max_batch_msgs = 1;
             }
             S->stats.max_queue = std::max<uint64_t>(S->stats.max_queue, S->queue.size());
+            publish_diagnostics(S);
         }
         inflight = !S->rinflight[0].empty() || !S->rinflight[1].empty();
         if (inflight && !S->rlive) {  // published work and no kernel: (re)launch
             const int rc = start_resident(S);
             {
-                std::lock_guard<std::mutex> lk(S->stats_mu);
+                SchedLock lk(S, S->stats_mu);
                 S->stats.batches++;  // resident mode: kernel launches
             }
             if (rc == AES_OK)
@@ -791,8 +915,18 @@ static int enqueue(aes_server* S, const aes_server_request& r, double arrival) {
 }
 
 static void producer_main(aes_server* S) {
+    if (S->cfg.flags & AES_SERVER_PIN_THREADS) S->producer_cpu = pin_thread(1);
     const double start = S->now();
     S->replay_start = start;
+    // Lateness diagnostics: the thread's involuntary switches are read every
+    // 16th hand-over and at any hand-over 20 us late or more.
+    double cpu0 = 0;
+    long inv_begin = 0, inv_prev = 0;
+    ThreadWatch::usage(&cpu0, &inv_begin);
+    inv_prev = inv_begin;
+    uint64_t handovers = 0;
+    double late_max = 0;
+    long late_invol = 0;
     std::vector<Pending> due_now;
     const size_t n = S->replay_reqs.size();
     // Hands request r (already checked: rc) to the scheduler's batch, or
@@ -831,6 +965,29 @@ static void producer_main(aes_server* S) {
         for (; i < n && start + S->replay_reqs[i].arrival_s <= now; ++i)
             take(S->replay_reqs[i], check_request(S, S->replay_reqs[i]));
         push_inbox(S, due_now.data(), due_now.size());
+        const double late = now - due;
+        if (++handovers % 16 == 0 || late >= 20e-6) {
+            double cpu;
+            long inv;
+            ThreadWatch::usage(&cpu, &inv);
+            if (late > late_max) {
+                late_max = late;
+                late_invol = inv - inv_prev;
+            }
+            inv_prev = inv;
+        }
+    }
+    {
+        double cpu;
+        long inv;
+        ThreadWatch::usage(&cpu, &inv);
+        std::lock_guard<std::mutex> lk(S->stats_mu);
+        if (late_max > 1e-9 * S->stats.producer_late_max_ns) {
+            S->stats.producer_late_max_ns = (uint64_t)(1e9 * late_max);
+            S->stats.producer_late_invol = (uint64_t)late_invol;
+        }
+        S->stats.producer_invol += (uint64_t)(inv - inv_begin);
+        S->stats.producer_cpu = S->producer_cpu;
     }
     S->producer_running.store(false);
 }
@@ -907,6 +1064,7 @@ static int setup_resident(aes_server* S) {
     S->rargs.tiles = (const ResTile*)(dev_view + sizeof(ResCtrl));
     S->rargs.cq = (ResDone*)(dev_view + sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt);
     S->rargs.cq_size = cq;
+    S->rargs.cq_log2 = (uint32_t)__builtin_ctz(cq);
     S->rargs.keys = S->dev_keys;
     S->rargs.err = S->status;
     S->rargs.ring_tiles = rt;
@@ -945,9 +1103,14 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
     if (cfg.resident_restart_pct == 0) cfg.resident_restart_pct = 80;
     if (cfg.nstreams < 1 || cfg.nstreams > 64 || cfg.threads < 64 || cfg.threads > 1024 || cfg.threads % 32 ||
         (cfg.blocks_per_thread != 1 && cfg.blocks_per_thread != 2 && cfg.blocks_per_thread != 4) ||
-        cfg.max_batch_msgs > (1u << 20) || (cfg.flags & ~(AES_SERVER_DRYRUN | AES_SERVER_RESIDENT)) ||
+        cfg.max_batch_msgs > (1u << 20) || (cfg.flags & ~(AES_SERVER_DRYRUN | AES_SERVER_RESIDENT | AES_SERVER_PIN_THREADS)) ||
         cfg.resident_restart_pct > 1000) {
         fail(AES_ERR_ARG, "invalid server configuration");
+        return nullptr;
+    }
+    if ((cfg.flags & AES_SERVER_RESIDENT) && cfg.threads > (int)kResidentMaxThreads) {
+        fail(AES_ERR_ARG, "resident mode: threads %d (at most %u compute threads per CTA)", cfg.threads,
+             kResidentMaxThreads);
         return nullptr;
     }
     const uint64_t res_tile = (uint64_t)cfg.threads * (uint64_t)cfg.blocks_per_thread;
@@ -1011,6 +1174,8 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
         return nullptr;
     }
     S->stats.budget_bytes = cfg.budget_bytes;
+    S->stats.sched_cpu = -1;
+    S->stats.producer_cpu = -1;
     S->t0 = std::chrono::steady_clock::now();
     S->magic = kServerMagic;
     S->scheduler = std::thread(S->resident ? scheduler_resident : scheduler_main, S);

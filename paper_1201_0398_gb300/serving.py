@@ -18,7 +18,7 @@ GiB = 1 << 30
 def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8 << 30, nkeys: int = 1024,
         nstreams: int = 4, threads: int = 0, blocks_per_thread: int = 0, max_batch_msgs: int = 4096,
         pool_bytes: int = GiB, check_last: int = 1000, seed: int = workloads.SEED_SERVE,
-        resident: bool = False) -> dict:
+        resident: bool = False, pin_threads: bool = False) -> dict:
     import torch
 
     w = workloads.serve_workload(rate=rate, duration_s=duration_s, nkeys=nkeys, seed=seed)
@@ -45,7 +45,8 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
 
     torch.cuda.synchronize()  # inputs complete before the first request
     srv = Server(keys, budget_bytes=budget_bytes, nstreams=nstreams, threads=threads,
-                 blocks_per_thread=blocks_per_thread, max_batch_msgs=max_batch_msgs, resident=resident)
+                 blocks_per_thread=blocks_per_thread, max_batch_msgs=max_batch_msgs, resident=resident,
+                 pin_threads=pin_threads)
     srv.replay(reqs)
     srv.replay_join()
     srv.drain(120.0)
@@ -85,6 +86,17 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
         "max_queue": int(stats["max_queue"]), "max_inflight_bytes": int(stats["max_inflight_bytes"]),
         "budget_bytes": int(budget_bytes), "nstreams": nstreams, "shape": f"{threads or 512}x{blocks_per_thread or (2 if resident else 1)}",
         "checked_alone": int(len(idx)), "mismatches": mismatches,
+        "host_threads": {
+            "pinned_cpus": [int(stats["sched_cpu"]), int(stats["producer_cpu"])],
+            "sched_passes": int(stats["sched_passes"]),
+            "sched_worst_window_us": stats["sched_worst_window_ns"] / 1e3,
+            "sched_worst_window_cpu_us": stats["sched_worst_window_cpu_ns"] / 1e3,
+            "sched_worst_window_invol": int(stats["sched_worst_window_invol"]),
+            "sched_invol": int(stats["sched_invol"]),
+            "sched_lock_wait_max_us": stats["sched_lock_wait_max_ns"] / 1e3,
+            "producer_late_max_us": stats["producer_late_max_ns"] / 1e3,
+            "producer_late_invol": int(stats["producer_late_invol"]),
+            "producer_invol": int(stats["producer_invol"])},
         "workload": f"Poisson {rate:.0f} req/s for {duration_s:g} s, sizes log-uniform 64 B-1 MiB (x16 B), "
                     f"{nkeys} resident keys (128/192/256), encrypt/decrypt 50/50, {budget_bytes >> 30} GiB budget",
     }

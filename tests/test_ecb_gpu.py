@@ -334,3 +334,56 @@ def test_one_gib_every_tuner_shape(gbaes, shape):
         del out
     del x
     torch.cuda.empty_cache()
+
+
+def compact_sizes():
+    """Sizes around the compact kernel's shapes: one warp, warps spread one per
+    SM, 8 warps per CTA, the grid cap (8 CTAs per SM) with a grid-stride tail."""
+    w = 32
+    return sorted({1, 2, 31, 32, 33, 255, 256, 257, sms() * w - 1, sms() * w, sms() * w + 1,
+                   sms() * 8 * w + 3, 8 * sms() * 8 * w - 1, 8 * sms() * 8 * w + 1000})
+
+
+@pytest.mark.parametrize("bits", BITS)
+def test_compact_tables_vs_oracle(gbaes, bits):
+    """The compact-table kernel (each table stored once) in every mode."""
+    rng = np.random.default_rng(1300 + bits)
+    key = rng.integers(0, 256, bits // 8, dtype=np.uint8).tobytes()
+    iv = rng.integers(0, 256, 16, dtype=np.uint8).tobytes()
+    k = gbaes.Key(key)
+    for n in compact_sizes():
+        data = rng.integers(0, 256, 16 * n, dtype=np.uint8)
+        x = dev(data)
+        for decrypt in (False, True):
+            out = gbaes.ecb_ex(k, x, decrypt=decrypt, kernel=gbaes.KERNEL_TABLE_COMPACT)
+            assert np.array_equal(host(out), oracle.ecb(key, bits, data, decrypt=decrypt)), (n, decrypt)
+        if n <= 128 * sms():  # CTR and CBC decryption take the compact tables for calls this small
+            for kind in (oracle.CTR_BE128, oracle.CTR_LE32_CARRY):
+                assert np.array_equal(host(gbaes.ctr_xcrypt(k, iv, x, kind=kind)),
+                                      oracle.ctr(key, bits, iv, data, kind)), (n, kind)
+            assert np.array_equal(host(gbaes.cbc_decrypt(k, iv, x)), oracle.cbc_decrypt(key, bits, iv, data)), n
+    assert gbaes.device_status() == 0
+
+
+@pytest.mark.parametrize("decrypt", (False, True))
+def test_size_dispatch_and_balanced_shapes_vs_oracle(gbaes, decrypt):
+    """AES_KERNEL_TABLE picks compact tables for small calls and the replicated
+    tables above; the replicated kernel shrinks its CTAs so that calls of a few
+    tiles per SM spread evenly.  Sizes on both sides of the switch and across
+    the shrinking range, through the default call and both variants forced."""
+    rng = np.random.default_rng(1400 + decrypt)
+    s = sms()
+    for bits in (128, 256):
+        key = rng.integers(0, 256, bits // 8, dtype=np.uint8).tobytes()
+        k = gbaes.Key(key)
+        for n in (128 * s - 1, 128 * s, 128 * s + 1, 65536, 3 * s * 1024 + 7, 262144, (1 << 20) + 13):
+            data = rng.integers(0, 256, 16 * n, dtype=np.uint8)
+            want = oracle.ecb(key, bits, data, decrypt=decrypt)
+            x = dev(data)
+            out = (gbaes.decrypt_ecb if decrypt else gbaes.encrypt_ecb)(k, x)
+            assert np.array_equal(host(out), want), n
+            for kid in (gbaes.KERNEL_TABLE_REPLICATED, gbaes.KERNEL_TABLE_COMPACT):
+                for bpt in (1, 2, 4):
+                    out = gbaes.ecb_ex(k, x, decrypt=decrypt, kernel=kid, blocks_per_thread=bpt)
+                    assert np.array_equal(host(out), want), (n, kid, bpt)
+    assert gbaes.device_status() == 0

@@ -336,7 +336,7 @@ def test_server_batches_overlap_on_device(gbaes):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("threads,bpt,ring_tiles,ring_items", [(512, 1, 0, 0), (256, 2, 256, 64), (1024, 4, 64, 16)])
+@pytest.mark.parametrize("threads,bpt,ring_tiles,ring_items", [(512, 1, 0, 0), (256, 2, 256, 64), (512, 4, 64, 16)])
 def test_resident_results_equal_alone_and_oracle(gbaes, threads, bpt, ring_tiles, ring_items):
     """Resident mode: 4,000 requests (64 B - 256 KiB, 64 keys of all sizes, both
     directions) at 100k req/s through one kernel that stays on the GPU; small
@@ -530,3 +530,38 @@ def test_resident_recovery_after_kernel_bound(gbaes):
         k = int(reqs["key_index"][i])
         assert np.array_equal(ys[b:b + n], oracle.ecb(raw_keys[k], int(bits[k]), xs[a:a + n], decrypt=bool(reqs["decrypt"][i])))
     assert gbaes.device_status() == 0
+
+
+@pytest.mark.parametrize("resident", (False, True))
+def test_dryrun_thread_diagnostics_and_pinning(gbaes, resident):
+    """Host-thread diagnostics after a replay (both modes): scheduler passes
+    and windows, lock waits, replay lateness; with pin_threads the scheduler
+    and replay threads sit on distinct CPUs of the process's affinity set."""
+    import os
+
+    allowed = sorted(os.sched_getaffinity(0))
+    srv = gbaes.Server(keyset(gbaes), dryrun=True, resident=resident, threads=64, blocks_per_thread=1,
+                       pin_threads=True)
+    rng = np.random.default_rng(11)
+    reqs = fake_requests(gbaes, 3000, rng, max_blocks=32, rate=100_000.0)
+    srv.replay(reqs)
+    srv.replay_join()
+    srv.drain(30.0)
+    assert len(srv.poll_all()) == 3000
+    st = srv.stats()
+    srv.close()
+    assert st["sched_passes"] > 0
+    assert st["sched_worst_window_ns"] > 0
+    assert st["sched_worst_window_cpu_ns"] <= st["sched_worst_window_ns"] + 10_000_000  # CPU clock: 1-10 ms ticks
+    assert st["producer_late_max_ns"] > 0
+    assert st["sched_cpu"] == allowed[-1]
+    assert st["producer_cpu"] == (allowed[-2] if len(allowed) > 1 else -1)
+
+
+def test_dryrun_unpinned_threads_report_no_cpu(gbaes):
+    srv = gbaes.Server(keyset(gbaes), dryrun=True)
+    srv.submit(1, 0, 1 << 20, 2 << 20, 4)
+    srv.drain(10.0)
+    st = srv.stats()
+    srv.close()
+    assert st["sched_cpu"] == -1 and st["producer_cpu"] == -1
