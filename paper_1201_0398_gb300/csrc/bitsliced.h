@@ -6,24 +6,25 @@
 // Section 2.1's layout) and bit t of that byte.  Every AES step is then plain
 // bitwise logic on planes, with no table lookups:
 //
-//  * SubBytes: the multiplicative inverse in GF(2^8) computed in the tower
-//    field GF((2^4)^2).  A byte a = ah*Y + al with ah, al in GF(2^4) =
-//    GF(2)[z]/(z^4+z+1) and Y^2 = Y + lambda has inverse
-//        a^-1 = (ah * d^-1) Y + ((ah + al) * d^-1),  d = lambda*ah^2 + ah*al + al^2,
-//    and d^-1 in GF(2^4) is four 4-input Boolean functions (3 LOP3 each, truth
-//    tables computed at compile time).  The change of basis between
-//    the AES field and the tower field is a linear map found at compile time
-//    (make_tower below) and merged with the S-box's affine map.  The affine
-//    constant 0x63 is not applied here: it passes unchanged through ShiftRows
-//    and MixColumns (each MixColumns row sums to 1), so the caller XORs it into
-//    the round keys instead.
+//  * SubBytes: the depth-16 S-box circuit of J. Boyar and R. Peralta ("A
+//    depth-16 circuit for the AES S-box", 2012): a linear layer of XORs into 27
+//    intermediate sums, a shared nonlinear middle of ANDs and XORs (the inverse
+//    in a tower of subfields, 34 ANDs as written here) and a bottom linear layer
+//    that also applies the S-box's affine map.  The affine constant 0x63 (the
+//    circuit's XNORs) is not applied here: it passes unchanged through
+//    ShiftRows and MixColumns (each MixColumns row sums to 1), so the caller
+//    XORs it into the round keys instead.
+//  * The inverse S-box reuses the same circuit: with F(z) = A inv(z) (the
+//    circuit without the constant, A the affine matrix), the inverse S-box of
+//    y is inv(A^-1 (y ^ 0x63)) = A^-1 F(A^-1 (y ^ 0x63)), the XOR with 0x63
+//    again folded into the round keys; A^-1 costs one three-input XOR per bit.
 //  * ShiftRows is a renaming of planes; MixColumns and AddRoundKey are XORs;
 //    InvMixColumns is MixColumns after the preprocessing
 //    a0 ^= 4(a0^a2), a2 ^= 4(a0^a2), a1 ^= 4(a1^a3), a3 ^= 4(a1^a3).
 //
-// The derivation is checked exhaustively at compile time against the S-box of
-// aes_tables.h (static_asserts at the end of this file).  Everything here is
-// plain C++ usable on the host as well as on the device.
+// The circuit is checked exhaustively at compile time against the S-box of
+// aes_tables.h (static_asserts below).  Everything here is plain C++ usable on
+// the host as well as on the device.
 #pragma once
 
 #include <cstdint>
@@ -41,48 +42,7 @@ namespace bs {
 
 // ---------------------------------------------------------- scalar helpers
 
-constexpr uint8_t gf16_mul(uint8_t a, uint8_t b) {  // GF(2)[z]/(z^4+z+1)
-    uint8_t p = 0;
-    for (int i = 0; i < 4; ++i)
-        if ((b >> i) & 1) p ^= (uint8_t)(a << i);
-    for (int d = 6; d >= 4; --d)
-        if ((p >> d) & 1) p ^= (uint8_t)(0x13 << (d - 4));
-    return p & 15;
-}
-
-constexpr uint8_t gf16_inv(uint8_t a) {  // a^14
-    uint8_t r = 1;
-    for (int i = 0; i < 14; ++i) r = gf16_mul(r, a);
-    return a ? r : 0;
-}
-
-constexpr uint8_t gf256_pow(uint8_t a, int e) {
-    uint8_t r = 1;
-    for (int i = 0; i < e; ++i) r = gf_mul_log(r, a);
-    return r;
-}
-
-// Applies an 8x8 GF(2) matrix given as rows (bit j of row i = M[i][j]).
-constexpr uint8_t apply8(const uint8_t (&rows)[8], uint8_t x) {
-    uint8_t y = 0;
-    for (int i = 0; i < 8; ++i) {
-        uint8_t v = rows[i] & x, par = 0;
-        for (int j = 0; j < 8; ++j) par ^= (v >> j) & 1;
-        y |= (uint8_t)(par << i);
-    }
-    return y;
-}
-
-struct Tower {
-    uint8_t lambda;         // Y^2 + Y + lambda irreducible over GF(16)
-    uint8_t enc_in[8];      // AES byte -> tower (bits 0..3 = al, 4..7 = ah)
-    uint8_t enc_out[8];     // tower -> AES byte, then the affine matrix (no constant)
-    uint8_t dec_in[8];      // AES byte -> inverse affine matrix (no constant) -> tower
-    uint8_t dec_out[8];     // tower -> AES byte
-    bool ok;
-};
-
-// Inverts an 8x8 GF(2) matrix (rows); ok=false if singular.
+// Inverts an 8x8 GF(2) matrix (rows: bit j of row i = M[i][j]); false if singular.
 constexpr bool invert8(const uint8_t (&m)[8], uint8_t (&inv)[8]) {
     uint8_t a[8] = {}, b[8] = {};
     for (int i = 0; i < 8; ++i) {
@@ -109,108 +69,70 @@ constexpr bool invert8(const uint8_t (&m)[8], uint8_t (&inv)[8]) {
     return true;
 }
 
-// Rows of the matrix whose columns are the given bytes (column j = image of bit j).
-constexpr void rows_from_columns(const uint8_t (&cols)[8], uint8_t (&rows)[8]) {
-    for (int i = 0; i < 8; ++i) {
-        uint8_t r = 0;
-        for (int j = 0; j < 8; ++j) r |= (uint8_t)(((cols[j] >> i) & 1) << j);
-        rows[i] = r;
-    }
-}
+struct Rows8 {
+    uint8_t r[8];
+    bool ok;
+};
 
-constexpr void mat_mul8(const uint8_t (&a)[8], const uint8_t (&b)[8], uint8_t (&c)[8]) {  // c = a * b
-    uint8_t cols[8] = {};
-    for (int j = 0; j < 8; ++j) cols[j] = apply8(a, apply8(b, (uint8_t)(1u << j)));
-    rows_from_columns(cols, c);
-}
-
-constexpr Tower make_tower() {
-    Tower T{};
-    // omega: a root of z^4 + z + 1 in the AES field (generates the subfield GF(16)).
-    uint8_t omega = 0;
-    for (int x = 2; x < 256 && !omega; ++x)
-        if ((gf256_pow((uint8_t)x, 4) ^ (uint8_t)x ^ 1) == 0) omega = (uint8_t)x;
-    // lambda: smallest with Y^2 + Y + lambda irreducible over GF(16).
-    for (int l = 1; l < 16 && !T.lambda; ++l) {
-        bool root = false;
-        for (int y = 0; y < 16; ++y)
-            if ((gf16_mul((uint8_t)y, (uint8_t)y) ^ (uint8_t)y ^ (uint8_t)l) == 0) root = true;
-        if (!root) T.lambda = (uint8_t)l;
-    }
-    uint8_t lam256 = 0;  // lambda written in the AES field: sum lambda_i omega^i
-    for (int i = 0; i < 4; ++i)
-        if ((T.lambda >> i) & 1) lam256 ^= gf256_pow(omega, i);
-    uint8_t beta = 0;  // a root of Y^2 + Y + lambda in the AES field
-    for (int x = 2; x < 256 && !beta; ++x)
-        if ((gf_mul_log((uint8_t)x, (uint8_t)x) ^ (uint8_t)x ^ lam256) == 0) beta = (uint8_t)x;
-    // tower bit j -> AES element: bits 0..3 are al (omega^j), bits 4..7 are ah (omega^(j-4) * beta)
-    uint8_t cols[8] = {};
-    for (int j = 0; j < 4; ++j) {
-        cols[j] = gf256_pow(omega, j);
-        cols[4 + j] = gf_mul_log(gf256_pow(omega, j), beta);
-    }
-    uint8_t to_aes[8] = {}, to_tower[8] = {};
-    rows_from_columns(cols, to_aes);
-    T.ok = omega && T.lambda && beta && invert8(to_aes, to_tower);
-    // affine matrix A: b'_i = b_i ^ b_{i+4} ^ b_{i+5} ^ b_{i+6} ^ b_{i+7}
+// The inverse of the S-box's affine matrix A (b'_i = b_i ^ b_{i+4} ^ b_{i+5} ^ b_{i+6} ^ b_{i+7}).
+constexpr Rows8 make_affine_inverse() {
     uint8_t A[8] = {}, Ainv[8] = {};
     for (int i = 0; i < 8; ++i)
         A[i] = (uint8_t)((1u << i) | (1u << ((i + 4) & 7)) | (1u << ((i + 5) & 7)) | (1u << ((i + 6) & 7)) |
                          (1u << ((i + 7) & 7)));
-    T.ok = T.ok && invert8(A, Ainv);
-    for (int i = 0; i < 8; ++i) {
-        T.enc_in[i] = to_tower[i];
-        T.dec_out[i] = to_aes[i];
-    }
-    mat_mul8(A, to_aes, T.enc_out);
-    mat_mul8(to_tower, Ainv, T.dec_in);
-    return T;
-}
-
-inline constexpr Tower kTower = make_tower();
-
-// Scalar model of the circuit (compile-time check only).
-constexpr uint8_t tower_inverse(uint8_t t) {
-    const uint8_t al = t & 15, ah = t >> 4;
-    const uint8_t d = gf16_mul(kTower.lambda, gf16_mul(ah, ah)) ^ gf16_mul(ah, al) ^ gf16_mul(al, al);
-    const uint8_t di = gf16_inv(d);
-    return (uint8_t)((gf16_mul(ah, di) << 4) | gf16_mul(ah ^ al, di));
-}
-
-constexpr bool check_tower() {
-    if (!kTower.ok) return false;
-    for (int x = 0; x < 256; ++x) {
-        if ((apply8(kTower.enc_out, tower_inverse(apply8(kTower.enc_in, (uint8_t)x))) ^ 0x63) != kAesTables.sbox[x])
-            return false;
-        if (apply8(kTower.dec_out, tower_inverse(apply8(kTower.dec_in, (uint8_t)(x ^ 0x63)))) !=
-            kAesTables.inv_sbox[x])
-            return false;
-    }
-    return true;
-}
-static_assert(check_tower(), "tower-field S-box circuit does not reproduce the S-box");
-
-// ------------------------------------------------------------ plane circuits
-
-// The four constant matrices, by value (device code sees only constants).
-struct Rows8 {
-    uint8_t r[8];
-};
-enum : int { kEncIn = 0, kEncOut = 1, kDecIn = 2, kDecOut = 3 };
-constexpr Rows8 tower_rows(int which) {
     Rows8 m{};
-    for (int i = 0; i < 8; ++i)
-        m.r[i] = which == kEncIn ? kTower.enc_in[i]
-                 : which == kEncOut ? kTower.enc_out[i]
-                 : which == kDecIn ? kTower.dec_in[i]
-                                   : kTower.dec_out[i];
+    m.ok = invert8(A, Ainv);
+    for (int i = 0; i < 8; ++i) m.r[i] = Ainv[i];
     return m;
 }
 
-// y = M x over 8 planes, M constant (rows): only the XORs M selects survive.
-template <int WHICH>
-GBAES_HD inline void lin8(const uint32_t (&x)[8], uint32_t (&y)[8]) {
-    constexpr Rows8 M = tower_rows(WHICH);
+// ------------------------------------------------------------ plane circuits
+
+// The S-box circuit without its affine constant: s = A inv(u) on planes, with
+// u[i], s[i] = bit 7 - i of the input and output bytes (i = 0: the most
+// significant bit), the bit order the published circuit is written in.
+GBAES_HD constexpr void sbox_circuit(const uint32_t (&u)[8], uint32_t (&s)[8]) {
+    // top linear layer
+    const uint32_t t1 = u[0] ^ u[3], t2 = u[0] ^ u[5], t3 = u[0] ^ u[6], t4 = u[3] ^ u[5], t5 = u[4] ^ u[6];
+    const uint32_t t6 = t1 ^ t5, t7 = u[1] ^ u[2], t8 = u[7] ^ t6, t9 = u[7] ^ t7, t10 = t6 ^ t7;
+    const uint32_t t11 = u[1] ^ u[5], t12 = u[2] ^ u[5], t13 = t3 ^ t4, t14 = t6 ^ t11, t15 = t5 ^ t11;
+    const uint32_t t16 = t5 ^ t12, t17 = t9 ^ t16, t18 = u[3] ^ u[7], t19 = t7 ^ t18, t20 = t1 ^ t19;
+    const uint32_t t21 = u[6] ^ u[7], t22 = t7 ^ t21, t23 = t2 ^ t22, t24 = t2 ^ t10, t25 = t20 ^ t17;
+    const uint32_t t26 = t3 ^ t16, t27 = t1 ^ t12;
+    // nonlinear middle
+    const uint32_t m1 = t13 & t6, m2 = t23 & t8, m3 = t14 ^ m1, m4 = t19 & u[7], m5 = m4 ^ m1;
+    const uint32_t m6 = t3 & t16, m7 = t22 & t9, m8 = t26 ^ m6, m9 = t20 & t17, m10 = m9 ^ m6;
+    const uint32_t m11 = t1 & t15, m12 = t4 & t27, m13 = m12 ^ m11, m14 = t2 & t10, m15 = m14 ^ m11;
+    const uint32_t m16 = m3 ^ m2, m17 = m5 ^ t24, m18 = m8 ^ m7, m19 = m10 ^ m15, m20 = m16 ^ m13;
+    const uint32_t m21 = m17 ^ m15, m22 = m18 ^ m13, m23 = m19 ^ t25, m24 = m22 ^ m23, m25 = m22 & m20;
+    const uint32_t m26 = m21 ^ m25, m27 = m20 ^ m21, m28 = m23 ^ m25, m29 = m28 & m27, m30 = m26 & m24;
+    const uint32_t m31 = m20 & m23, m32 = m27 ^ m25, m33 = m27 & m31, m34 = m24 ^ m25, m35 = m21 & m22;
+    const uint32_t m36 = m24 & m35, m37 = m21 ^ m29, m38 = m32 ^ m33, m39 = m23 ^ m30, m40 = m34 ^ m36;
+    const uint32_t m41 = m38 ^ m40, m42 = m37 ^ m39, m43 = m37 ^ m38, m44 = m39 ^ m40, m45 = m42 ^ m41;
+    const uint32_t m46 = m44 & t6, m47 = m40 & t8, m48 = m39 & u[7], m49 = m43 & t16, m50 = m38 & t9;
+    const uint32_t m51 = m37 & t17, m52 = m42 & t15, m53 = m45 & t27, m54 = m41 & t10, m55 = m44 & t13;
+    const uint32_t m56 = m40 & t23, m57 = m39 & t19, m58 = m43 & t3, m59 = m38 & t22, m60 = m37 & t20;
+    const uint32_t m61 = m42 & t1, m62 = m45 & t4, m63 = m41 & t2;
+    // bottom linear layer (the affine map; its constant is left to the round keys)
+    const uint32_t l0 = m61 ^ m62, l1 = m50 ^ m56, l2 = m46 ^ m48, l3 = m47 ^ m55, l4 = m54 ^ m58;
+    const uint32_t l5 = m49 ^ m61, l6 = m62 ^ l5, l7 = m46 ^ l3, l8 = m51 ^ m59, l9 = m52 ^ m53;
+    const uint32_t l10 = m53 ^ l4, l11 = m60 ^ l2, l12 = m48 ^ m51, l13 = m50 ^ l0, l14 = m52 ^ m61;
+    const uint32_t l15 = m55 ^ l1, l16 = m56 ^ l0, l17 = m57 ^ l1, l18 = m58 ^ l8, l19 = m63 ^ l4;
+    const uint32_t l20 = l0 ^ l1, l21 = l1 ^ l7, l22 = l3 ^ l12, l23 = l18 ^ l2, l24 = l15 ^ l9;
+    const uint32_t l25 = l6 ^ l10, l26 = l7 ^ l9, l27 = l8 ^ l10, l28 = l11 ^ l14, l29 = l11 ^ l17;
+    s[0] = l6 ^ l24;
+    s[1] = l16 ^ l26;
+    s[2] = l19 ^ l28;
+    s[3] = l6 ^ l21;
+    s[4] = l20 ^ l22;
+    s[5] = l25 ^ l29;
+    s[6] = l13 ^ l27;
+    s[7] = l6 ^ l23;
+}
+
+// y = A^-1 x over 8 planes (x[t] = bit t): only the XORs the rows select survive.
+GBAES_HD constexpr void affine_inverse_planes(const uint32_t (&x)[8], uint32_t (&y)[8]) {
+    constexpr Rows8 M = make_affine_inverse();  // (a constant in device code too)
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         uint32_t acc = 0;
@@ -221,126 +143,59 @@ GBAES_HD inline void lin8(const uint32_t (&x)[8], uint32_t (&y)[8]) {
     }
 }
 
-// GF(16) product of plane quadruples (polynomial basis, z^4 = z + 1).
-GBAES_HD inline void mul16(const uint32_t* a, const uint32_t* b, uint32_t* c) {
-    const uint32_t p0 = a[0] & b[0];
-    const uint32_t p1 = (a[0] & b[1]) ^ (a[1] & b[0]);
-    const uint32_t p2 = (a[0] & b[2]) ^ (a[1] & b[1]) ^ (a[2] & b[0]);
-    const uint32_t p3 = (a[0] & b[3]) ^ (a[1] & b[2]) ^ (a[2] & b[1]) ^ (a[3] & b[0]);
-    const uint32_t p4 = (a[1] & b[3]) ^ (a[2] & b[2]) ^ (a[3] & b[1]);
-    const uint32_t p5 = (a[2] & b[3]) ^ (a[3] & b[2]);
-    const uint32_t p6 = a[3] & b[3];
-    c[0] = p0 ^ p4;
-    c[1] = p1 ^ p4 ^ p5;
-    c[2] = p2 ^ p5 ^ p6;
-    c[3] = p3 ^ p6;
-}
-
-// a^2 in GF(16): (a0 + a1 z + a2 z^2 + a3 z^3)^2 = (a0^a2) + a2 z + (a1^a3) z^2 + a3 z^3.
-GBAES_HD inline void sq16(const uint32_t* a, uint32_t* c) {
-    c[0] = a[0] ^ a[2];
-    c[1] = a[2];
-    c[2] = a[1] ^ a[3];
-    c[3] = a[3];
-}
-
-// Product with the constant lambda (bits select which shifted copies are added).
-GBAES_HD inline void mul16_lambda(const uint32_t* a, uint32_t* c) {
-    constexpr uint8_t lam = kTower.lambda;
-    uint32_t l[4];
+// S-box without its affine constant, in place on one byte's 8 planes (x[t] = bit t).
+GBAES_HD constexpr void sbox_planes(uint32_t* x) {
+    uint32_t u[8] = {}, o[8] = {};
 #pragma unroll
-    for (int i = 0; i < 4; ++i) l[i] = ((lam >> i) & 1) ? 0xffffffffu : 0u;
-    mul16(a, l, c);
-}
-
-// Three-input Boolean function given by its truth table LUT (bit (a<<2|b<<1|c)
-// of LUT = f(a,b,c)), applied bitwise: one LOP3 on the device.
-template <int LUT>
-GBAES_HD inline uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
-#if defined(__CUDA_ARCH__)
-    uint32_t d;
-    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
-    return d;
-#else
-    uint32_t d = 0;
-    for (int k = 0; k < 8; ++k)
-        if ((LUT >> k) & 1)
-            d |= ((k & 4) ? a : ~a) & ((k & 2) ? b : ~b) & ((k & 1) ? c : ~c);
-    return d;
-#endif
-}
-
-// Truth table of output bit I of the GF(16) inverse restricted to input bit 3 = D3,
-// as a function of input bits (0, 1, 2) in LOP3 operand order (a, b, c).
-constexpr int inv16_lut(int I, int D3) {
-    int lut = 0;
-    for (int k = 0; k < 8; ++k) {
-        const int d = ((k >> 2) & 1) | (((k >> 1) & 1) << 1) | ((k & 1) << 2) | (D3 << 3);
-        lut |= ((gf16_inv((uint8_t)d) >> I) & 1) << k;
-    }
-    return lut;
-}
-
-// GF(16) inverse (0 -> 0) of a plane quadruple: each output bit is a
-// four-input function, i.e. two three-input LOP3s selected by d[3] (0xCA:
-// a ? b : c), 12 operations in all.
-GBAES_HD inline void inv16(const uint32_t* d, uint32_t* o) {
-#define GBAES_INV16_BIT(I)                                                   \
-    {                                                                        \
-        const uint32_t lo = lop3<inv16_lut(I, 0)>(d[0], d[1], d[2]);         \
-        const uint32_t hi = lop3<inv16_lut(I, 1)>(d[0], d[1], d[2]);         \
-        o[I] = lop3<0xCA>(d[3], hi, lo);                                     \
-    }
-    GBAES_INV16_BIT(0)
-    GBAES_INV16_BIT(1)
-    GBAES_INV16_BIT(2)
-    GBAES_INV16_BIT(3)
-#undef GBAES_INV16_BIT
-}
-
-// Inverse in GF(2^8) through the tower field, on tower coordinates t[0..7].
-GBAES_HD inline void tower_inv(const uint32_t (&t)[8], uint32_t (&o)[8]) {
-    const uint32_t* al = t;
-    const uint32_t* ah = t + 4;
-    uint32_t a2[4], la2[4], hl[4], l2[4], d[4];
-    sq16(ah, a2);
-    mul16_lambda(a2, la2);
-    mul16(ah, al, hl);
-    sq16(al, l2);
+    for (int i = 0; i < 8; ++i) u[i] = x[7 - i];
+    sbox_circuit(u, o);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) d[i] = la2[i] ^ hl[i] ^ l2[i];
-    uint32_t di[4];
-    inv16(d, di);
-    uint32_t s[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) s[i] = ah[i] ^ al[i];
-    mul16(s, di, o);       // low half: (ah + al) d^-1
-    mul16(ah, di, o + 4);  // high half: ah d^-1
+    for (int i = 0; i < 8; ++i) x[7 - i] = o[i];
 }
 
-// S-box without its affine constant, in place on one byte's 8 planes.
-GBAES_HD inline void sbox_planes(uint32_t* x) {
-    uint32_t in[8], t[8], o[8], y[8];
+// Inverse S-box for input already XORed with the affine constant, in place:
+// A^-1 F(A^-1 x), F the circuit.
+GBAES_HD constexpr void inv_sbox_planes(uint32_t* x) {
+    uint32_t in[8] = {}, z[8] = {}, u[8] = {}, o[8] = {}, f[8] = {}, y[8] = {};
 #pragma unroll
     for (int i = 0; i < 8; ++i) in[i] = x[i];
-    lin8<kEncIn>(in, t);
-    tower_inv(t, o);
-    lin8<kEncOut>(o, y);
+    affine_inverse_planes(in, z);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) u[i] = z[7 - i];
+    sbox_circuit(u, o);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) f[7 - i] = o[i];
+    affine_inverse_planes(f, y);
 #pragma unroll
     for (int i = 0; i < 8; ++i) x[i] = y[i];
 }
 
-// Inverse S-box for input already XORed with the affine constant, in place.
-GBAES_HD inline void inv_sbox_planes(uint32_t* x) {
-    uint32_t in[8], t[8], o[8], y[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) in[i] = x[i];
-    lin8<kDecIn>(in, t);
-    tower_inv(t, o);
-    lin8<kDecOut>(o, y);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) x[i] = y[i];
+// Exhaustive check: plane k of the input holds bit t of the byte value 32*g + k.
+constexpr bool check_sbox_circuit() {
+    if (!make_affine_inverse().ok) return false;
+    for (int g = 0; g < 8; ++g) {
+        uint32_t fwd[8] = {}, inv[8] = {};
+        for (int t = 0; t < 8; ++t)
+            for (int k = 0; k < 32; ++k) {
+                const int x = 32 * g + k;
+                fwd[t] |= (uint32_t)((x >> t) & 1) << k;
+                inv[t] |= (uint32_t)(((x ^ 0x63) >> t) & 1) << k;
+            }
+        sbox_planes(fwd);
+        inv_sbox_planes(inv);
+        for (int k = 0; k < 32; ++k) {
+            const int x = 32 * g + k;
+            int f = 0, i = 0;
+            for (int t = 0; t < 8; ++t) {
+                f |= (int)((fwd[t] >> k) & 1) << t;
+                i |= (int)((inv[t] >> k) & 1) << t;
+            }
+            if ((f ^ 0x63) != kAesTables.sbox[x] || i != kAesTables.inv_sbox[x]) return false;
+        }
+    }
+    return true;
 }
+static_assert(check_sbox_circuit(), "the S-box circuit does not reproduce the S-box");
 
 // Multiplication by {02} on one byte's planes (t[0] = least significant bit).
 GBAES_HD inline void xtime_planes(const uint32_t* a, uint32_t* y) {

@@ -1,5 +1,5 @@
 """The bitsliced circuit (csrc/bitsliced.h) compiled for the CPU by a test
-harness and compared with the oracle: transposes, the tower-field S-box, the
+harness and compared with the oracle: transposes, the S-box circuit, the
 folded affine constant, MixColumns / InvMixColumns and the key planes."""
 import os
 import subprocess
