@@ -87,6 +87,9 @@ def parse_args():
                    help="--serve-sweep: offered request rates (requests/s), comma separated")
     p.add_argument("--serve-sweep-modes", default="resident,launch",
                    help="--serve-sweep: server modes to run (resident, launch)")
+    p.add_argument("--serve-sweep-repeat", type=int, default=1, help="--serve-sweep: runs per point")
+    p.add_argument("--serve-poll-ms", type=float, default=0.0,
+                   help="--serve-sweep: take completions every this many ms during the replay (0: at the end)")
     p.add_argument("--serve-pin", action="store_true",
                    help="--serve-sweep: pin the server's scheduler and replay threads to their own CPUs")
     p.add_argument("--serve-sweep-shape", default="",
@@ -110,7 +113,7 @@ def kernel_fingerprint() -> str:
     """Hash of the table kernel's device code (host launcher code excluded)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1201_0398_gb300", "csrc")
-    for name in ("ecb_table.cu", "aes_rounds.cuh", "aes_tables.h", "gbaes_internal.h"):
+    for name in ("ecb_table.cu", "aes_rounds.cuh", "aes_tables.h"):
         with open(os.path.join(csrc, name), "rb") as f:
             text = f.read()
         if name == "ecb_table.cu":
@@ -779,11 +782,12 @@ def run_serve_sweep(args):
     load()
     modes = [m.strip() for m in args.serve_sweep_modes.split(",")]
     threads, bpt = (int(v) for v in args.serve_sweep_shape.split("x")) if args.serve_sweep_shape else (0, 0)
-    for rate in (float(r) for r in args.serve_sweep_rates.split(",")):
+    rates = [float(r) for r in args.serve_sweep_rates.split(",") for _ in range(args.serve_sweep_repeat)]
+    for rate in rates:
         for resident in (m == "resident" for m in modes):
             shape = dict(threads=threads, blocks_per_thread=bpt) if resident else {}
             r = serving.run(rate=rate, duration_s=args.serve_sweep_seconds, check_last=200, resident=resident,
-                            pin_threads=args.serve_pin, **shape)
+                            pin_threads=args.serve_pin, poll_every_s=args.serve_poll_ms / 1e3, **shape)
             torch.cuda.empty_cache()
             keep = ("mode", "value", "offered_gbs", "requests", "completed_ok", "p50_ms", "p99_ms", "p999_ms",
                     "max_ms", "p50_queue_ms", "p50_service_ms", "max_queue", "max_inflight_bytes", "shape",

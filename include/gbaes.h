@@ -314,22 +314,48 @@ typedef struct aes_server_stats {
     uint64_t max_batch_msgs;
     uint64_t budget_bytes;
     uint64_t recovered_tiles;    /* resident mode: tiles re-published after the kernel's own bound ended it */
-    /* Host-thread diagnostics, for latency tails: the scheduler thread, then the
-     * replay thread.  The scheduler reads its own CPU time and context-switch
-     * counts (getrusage) every 16 passes and after any pass that comes more than
-     * 50 us after the one before; between two readings lies a window. */
+} aes_server_stats;
+
+/* Host-thread diagnostics of a server, for latency tails.  Times in ns; the
+ * "_at_ns" fields say when the worst case happened, in ns on the server's clock
+ * (which starts at creation).  The scheduler reads its own CPU time,
+ * context-switch and page-fault counts (getrusage) every 16 passes and after
+ * any pass that comes more than 50 us after the one before; between two
+ * readings lies a window.  A window far longer than the CPU time in it, with
+ * involuntary switches, is time the thread was descheduled; with voluntary
+ * ones, time it blocked (a lock, a CUDA call, a page fault) or yielded. */
+typedef struct aes_server_diag {
     uint64_t sched_passes;              /* scheduler passes */
     uint64_t sched_worst_window_ns;     /* longest window in which the scheduler had work waiting throughout */
     uint64_t sched_worst_window_cpu_ns; /* CPU time the scheduler got in that window */
     uint64_t sched_worst_window_invol;  /* involuntary context switches (preemptions) in that window */
+    uint64_t sched_worst_window_vol;    /* voluntary context switches (blocking waits, yields) in that window */
+    uint64_t sched_worst_window_at_ns;  /* when that window began */
+    uint64_t sched_worst_window_minflt; /* page faults in that window: minor (no I/O), */
+    uint64_t sched_worst_window_majflt; /* and major */
     uint64_t sched_invol;               /* involuntary context switches of the scheduler over the server's life */
-    uint64_t sched_lock_wait_max_ns;    /* the scheduler's longest wait for a lock other threads share */
-    uint64_t producer_late_max_ns;      /* replay: latest hand-over of requests after the first one's arrival time */
-    uint64_t producer_late_invol;       /* replay: involuntary switches since the reading before that hand-over */
+    uint64_t lock_wait_max_ns[3];       /* the scheduler's longest wait for the submission, completion and stats locks */
+    uint64_t lock_wait_at_ns[3];
+    uint64_t cuda_call_max_ns;          /* the scheduler's longest CUDA call (event or stream query, launch) */
+    uint64_t cuda_call_at_ns;
+    uint64_t sched_phase_max_ns[5];     /* the scheduler's longest pass phase: taking submissions, completions,
+                                           kernel or event queries, admission, launches and statistics (in
+                                           launch-per-batch mode, completions count under the queries and
+                                           admission under launches) */
+    uint64_t sched_phase_at_ns[5];
+    uint64_t inbox_hold_max_ns[2];      /* longest hold of the submission lock: by the scheduler, by a submitter */
+    uint64_t producer_late_max_ns;      /* replay: latest hand-over after the first due request's arrival time */
+    uint64_t producer_late_at_ns;
+    uint64_t producer_late_invol;       /* replay: involuntary switches since the thread's reading before that */
     uint64_t producer_invol;            /* replay: involuntary context switches over all replays */
+    uint64_t producer_check_max_ns;     /* replay: longest host check of one request (driver pointer queries) */
+    uint64_t producer_check_at_ns;
     int64_t sched_cpu;                  /* CPU the scheduler thread is pinned to (AES_SERVER_PIN_THREADS), else -1 */
     int64_t producer_cpu;               /* CPU the replay thread is pinned to, else -1 */
-} aes_server_stats;
+} aes_server_diag;
+
+/* Copies the server's host-thread diagnostics. */
+int aes_server_get_diag(aes_server* server, aes_server_diag* out);
 
 /* Creates a server on the current device with nkeys resident key contexts
  * (copied; the caller may free them afterwards) and starts its scheduler

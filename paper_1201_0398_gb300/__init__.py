@@ -125,6 +125,7 @@ def _declare(lib):
         "aes_server_drain": (c.c_int, [vp, c.c_double]),
         "aes_server_poll": (c.c_int, [vp, vp, sz]),
         "aes_server_get_stats": (c.c_int, [vp, vp]),
+        "aes_server_get_diag": (c.c_int, [vp, vp]),
         "aes_server_inject_fault": (c.c_int, [vp, c.c_uint64]),
         "aes_server_cancel": (c.c_int, [vp, c.c_uint64]),
         "aes_server_destroy": (None, [vp]),
@@ -465,11 +466,21 @@ class _ServerConfig(ctypes.Structure):
 class _ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "rejected", "batches",
                                                "max_inflight_bytes", "max_queue", "max_batch_msgs", "budget_bytes",
-                                               "recovered_tiles", "sched_passes", "sched_worst_window_ns",
-                                               "sched_worst_window_cpu_ns", "sched_worst_window_invol", "sched_invol",
-                                               "sched_lock_wait_max_ns", "producer_late_max_ns",
-                                               "producer_late_invol", "producer_invol")] + [
-        ("sched_cpu", ctypes.c_int64), ("producer_cpu", ctypes.c_int64)]
+                                               "recovered_tiles")]
+
+
+class _ServerDiag(ctypes.Structure):
+    _fields_ = ([(n, ctypes.c_uint64) for n in ("sched_passes", "sched_worst_window_ns", "sched_worst_window_cpu_ns",
+                                                "sched_worst_window_invol", "sched_worst_window_vol",
+                                                "sched_worst_window_at_ns", "sched_worst_window_minflt",
+                                                "sched_worst_window_majflt", "sched_invol")] +
+                [("lock_wait_max_ns", ctypes.c_uint64 * 3), ("lock_wait_at_ns", ctypes.c_uint64 * 3)] +
+                [(n, ctypes.c_uint64) for n in ("cuda_call_max_ns", "cuda_call_at_ns")] +
+                [("sched_phase_max_ns", ctypes.c_uint64 * 5), ("sched_phase_at_ns", ctypes.c_uint64 * 5),
+                 ("inbox_hold_max_ns", ctypes.c_uint64 * 2)] +
+                [(n, ctypes.c_uint64) for n in ("producer_late_max_ns", "producer_late_at_ns", "producer_late_invol",
+                                                "producer_invol", "producer_check_max_ns", "producer_check_at_ns")] +
+                [("sched_cpu", ctypes.c_int64), ("producer_cpu", ctypes.c_int64)])
 
 
 class Server:
@@ -529,6 +540,16 @@ class Server:
         s = _ServerStats()
         _check(self._lib.aes_server_get_stats(self._h, ctypes.byref(s)))
         return {n: getattr(s, n) for n, _ in s._fields_}
+
+    def diag(self) -> dict:
+        """Host-thread diagnostics (aes_server_diag); lock waits by lock: submissions, completions, stats."""
+        d = _ServerDiag()
+        _check(self._lib.aes_server_get_diag(self._h, ctypes.byref(d)))
+        out = {}
+        for n, _ in d._fields_:
+            v = getattr(d, n)
+            out[n] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
 
     def cancel(self, req_id: int):
         """Cancels a request still waiting for admission (it completes with AES_ERR_STATE)."""

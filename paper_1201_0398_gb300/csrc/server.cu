@@ -91,37 +91,47 @@ struct ResItem {
 // time, with involuntary switches, is time the thread was descheduled.
 struct ThreadWatch {
     double win_start = 0, cpu_start = 0, prev_pass = 0;
-    long invol_start = 0;
+    long invol_start = 0, vol_start = 0, minflt_start = 0, majflt_start = 0;
     bool win_busy = true, started = false;
     uint32_t passes = 0;
     uint64_t npasses = 0;
-    double worst_wall = 0, worst_cpu = 0;
-    long worst_invol = 0, invol_total = 0;
+    double worst_wall = 0, worst_cpu = 0, worst_at = 0;
+    long worst_invol = 0, worst_vol = 0, worst_minflt = 0, worst_majflt = 0, invol_total = 0;
 
-    static void usage(double* cpu, long* invol) {
+    static void usage(double* cpu, long* invol, long* vol = nullptr, long* minflt = nullptr, long* majflt = nullptr) {
         struct rusage u;
         memset(&u, 0, sizeof u);
         getrusage(RUSAGE_THREAD, &u);
         *cpu = (double)u.ru_utime.tv_sec + 1e-6 * u.ru_utime.tv_usec + (double)u.ru_stime.tv_sec +
                1e-6 * u.ru_stime.tv_usec;
         *invol = u.ru_nivcsw;
+        if (vol) *vol = u.ru_nvcsw;
+        if (minflt) *minflt = u.ru_minflt;
+        if (majflt) *majflt = u.ru_majflt;
     }
     void sample(double now) {
         double cpu;
-        long invol;
-        usage(&cpu, &invol);
+        long invol, vol, minflt, majflt;
+        usage(&cpu, &invol, &vol, &minflt, &majflt);
         if (started) {
             invol_total += invol - invol_start;
             if (win_busy && now - win_start > worst_wall) {
                 worst_wall = now - win_start;
                 worst_cpu = cpu - cpu_start;
                 worst_invol = invol - invol_start;
+                worst_vol = vol - vol_start;
+                worst_minflt = minflt - minflt_start;
+                worst_majflt = majflt - majflt_start;
+                worst_at = win_start;
             }
         }
         started = true;
         win_start = now;
         cpu_start = cpu;
         invol_start = invol;
+        vol_start = vol;
+        minflt_start = minflt;
+        majflt_start = majflt;
         win_busy = true;
     }
     // A pass at `now`; busy: the thread had work waiting since its previous pass.
@@ -212,10 +222,12 @@ struct aes_server {
     // Host-thread diagnostics (aes_server_stats): the scheduler's, kept by the
     // scheduler thread; the replay thread's, kept by that thread.
     ThreadWatch sched_watch;
-    double lock_wait_max = 0;     // scheduler: longest wait for a lock shared with other threads
-    double late_max = 0;          // replay: latest hand-over after a request's scheduled arrival
-    long late_invol = 0;          // replay: involuntary switches in the window of that hand-over
-    long producer_invol = 0;      // replay: involuntary switches over the replays
+    double lock_wait_max[3] = {0, 0, 0}, lock_wait_at[3] = {0, 0, 0};  // submissions, completions, stats
+    double cuda_call_max = 0, cuda_call_at = 0;
+    double phase_max[5] = {0, 0, 0, 0, 0}, phase_at[5] = {0, 0, 0, 0, 0};  // scheduler pass phases
+    double inbox_hold_max = 0;                 // by the scheduler
+    std::atomic<uint64_t> submit_hold_ns{0};   // by a submitter (replay thread or aes_server_submit)
+    aes_server_diag diag{};       // published copy (stats_mu)
     int sched_cpu = -1, producer_cpu = -1;  // CPU each thread is pinned to (AES_SERVER_PIN_THREADS), or -1
     bool sched_slept = false;     // scheduler: its last idle wait slept on the condition variable
 
@@ -227,14 +239,20 @@ struct aes_server {
 namespace gbaes {
 
 // A lock taken by the scheduler thread on a mutex that other threads share;
-// the wait counts toward the scheduler's longest lock wait.
+// the wait counts toward the scheduler's longest wait for that lock.
+enum { kLockInbox = 0, kLockDone = 1, kLockStats = 2 };
+
 class SchedLock {
    public:
-    SchedLock(aes_server* S, std::mutex& m) : m_(m) {
+    SchedLock(aes_server* S, int which)
+        : m_(which == kLockInbox ? S->in_mu : which == kLockDone ? S->out_mu : S->stats_mu) {
         const auto t = std::chrono::steady_clock::now();
         m_.lock();
         const double w = std::chrono::duration<double>(std::chrono::steady_clock::now() - t).count();
-        if (w > S->lock_wait_max) S->lock_wait_max = w;
+        if (w > S->lock_wait_max[which]) {
+            S->lock_wait_max[which] = w;
+            S->lock_wait_at[which] = S->now();
+        }
     }
     ~SchedLock() { m_.unlock(); }
     SchedLock(const SchedLock&) = delete;
@@ -243,6 +261,32 @@ class SchedLock {
    private:
     std::mutex& m_;
 };
+
+// Times one CUDA call of the scheduler thread.
+template <class F>
+static auto timed_cuda(aes_server* S, F&& f) -> decltype(f()) {
+    const double t = S->now();
+    auto r = f();
+    const double d = S->now() - t;
+    if (d > S->cuda_call_max) {
+        S->cuda_call_max = d;
+        S->cuda_call_at = t;
+    }
+    return r;
+}
+
+// Scheduler pass phases: 0 submissions, 1 completions, 2 kernel or event
+// queries, 3 admission, 4 launch and statistics.  Ends phase i begun at *t.
+enum { kPhaseInbox = 0, kPhaseDone = 1, kPhaseQuery = 2, kPhaseAdmit = 3, kPhaseLaunch = 4 };
+
+static void end_phase(aes_server* S, int i, double* t) {
+    const double now = S->now();
+    if (now - *t > S->phase_max[i]) {
+        S->phase_max[i] = now - *t;
+        S->phase_at[i] = *t;
+    }
+    *t = now;
+}
 
 // Pins the calling thread to one CPU of the process's affinity set: the
 // last (which = 0) or the one before it (which = 1).  Returns the CPU or -1.
@@ -262,16 +306,32 @@ static int pin_thread(int which) {
     return -1;
 }
 
-// Copies the scheduler's diagnostics into the stats (caller holds stats_mu).
+// Copies the scheduler's diagnostics into the published copy (caller holds stats_mu).
 static void publish_diagnostics(aes_server* S) {
     const ThreadWatch& w = S->sched_watch;
-    S->stats.sched_passes = w.npasses;
-    S->stats.sched_worst_window_ns = (uint64_t)(1e9 * w.worst_wall);
-    S->stats.sched_worst_window_cpu_ns = (uint64_t)(1e9 * w.worst_cpu);
-    S->stats.sched_worst_window_invol = (uint64_t)w.worst_invol;
-    S->stats.sched_invol = (uint64_t)w.invol_total;
-    S->stats.sched_lock_wait_max_ns = (uint64_t)(1e9 * S->lock_wait_max);
-    S->stats.sched_cpu = S->sched_cpu;
+    aes_server_diag& d = S->diag;
+    d.sched_passes = w.npasses;
+    d.sched_worst_window_ns = (uint64_t)(1e9 * w.worst_wall);
+    d.sched_worst_window_cpu_ns = (uint64_t)(1e9 * w.worst_cpu);
+    d.sched_worst_window_invol = (uint64_t)w.worst_invol;
+    d.sched_worst_window_vol = (uint64_t)w.worst_vol;
+    d.sched_worst_window_at_ns = (uint64_t)(1e9 * w.worst_at);
+    d.sched_worst_window_minflt = (uint64_t)w.worst_minflt;
+    d.sched_worst_window_majflt = (uint64_t)w.worst_majflt;
+    d.sched_invol = (uint64_t)w.invol_total;
+    for (int i = 0; i < 3; ++i) {
+        d.lock_wait_max_ns[i] = (uint64_t)(1e9 * S->lock_wait_max[i]);
+        d.lock_wait_at_ns[i] = (uint64_t)(1e9 * S->lock_wait_at[i]);
+    }
+    d.cuda_call_max_ns = (uint64_t)(1e9 * S->cuda_call_max);
+    d.cuda_call_at_ns = (uint64_t)(1e9 * S->cuda_call_at);
+    for (int i = 0; i < 5; ++i) {
+        d.sched_phase_max_ns[i] = (uint64_t)(1e9 * S->phase_max[i]);
+        d.sched_phase_at_ns[i] = (uint64_t)(1e9 * S->phase_at[i]);
+    }
+    d.inbox_hold_max_ns[0] = (uint64_t)(1e9 * S->inbox_hold_max);
+    d.inbox_hold_max_ns[1] = S->submit_hold_ns.load(std::memory_order_relaxed);
+    d.sched_cpu = S->sched_cpu;
 }
 
 static void complete(aes_server* S, std::vector<Pending>& reqs, int status, double launch_s, double done_s) {
@@ -288,11 +348,11 @@ static void complete(aes_server* S, std::vector<Pending>& reqs, int status, doub
         out.push_back(c);
     }
     {
-        SchedLock lk(S, S->out_mu);
+        SchedLock lk(S, kLockDone);
         S->done.insert(S->done.end(), out.begin(), out.end());
     }
     {
-        SchedLock lk(S, S->stats_mu);
+        SchedLock lk(S, kLockStats);
         S->stats.completed += reqs.size();
         if (status != AES_OK) S->stats.failed += reqs.size();
     }
@@ -358,7 +418,8 @@ static bool take_inbox(aes_server* S) {
     if (S->inbox_n.load(std::memory_order_acquire) == 0 && !S->cancels_n.load(std::memory_order_acquire))
         return false;  // nothing new: leave the lock to the producers
     {
-        SchedLock lk(S, S->in_mu);
+        SchedLock lk(S, kLockInbox);
+        const double t = S->now();
         if (!S->inbox.empty()) {
             for (Pending& p : S->inbox) S->queue.push_back(p);
             S->inbox.clear();
@@ -367,6 +428,7 @@ static bool take_inbox(aes_server* S) {
         }
         cancels.swap(S->cancels);
         S->cancels_n.store(0, std::memory_order_release);
+        S->inbox_hold_max = std::max(S->inbox_hold_max, S->now() - t);
     }
     if (!cancels.empty()) {  // only requests not yet admitted can be cancelled
         std::vector<Pending> gone;
@@ -409,7 +471,9 @@ static void scheduler_main(aes_server* S) {
     for (;;) {
         S->sched_watch.pass(S->now(), !S->sched_slept);
         S->sched_slept = false;
+        double ph = S->now();
         bool worked = take_inbox(S);
+        end_phase(S, kPhaseInbox, &ph);
         // Completions.
         for (Slot& slot : S->slots) {
             if (!slot.busy) continue;
@@ -417,7 +481,7 @@ static void scheduler_main(aes_server* S) {
             if (S->dryrun) {
                 if (S->now() - slot.launch_s < 1e-6 * S->cfg.dryrun_batch_us) continue;
             } else {
-                cudaError_t q = cudaEventQuery(slot.done);
+                cudaError_t q = timed_cuda(S, [&] { return cudaEventQuery(slot.done); });
                 if (q == cudaErrorNotReady) continue;
                 if (q != cudaSuccess) st = AES_ERR_CUDA;
             }
@@ -428,6 +492,7 @@ static void scheduler_main(aes_server* S) {
             complete(S, slot.reqs, st, slot.launch_s, t);
             worked = true;
         }
+        end_phase(S, kPhaseQuery, &ph);  // (event queries and completions)
         // Admission in arrival order, then launch on free slots.
         for (Slot& slot : S->slots) {
             if (slot.busy || S->queue.empty()) continue;
@@ -444,10 +509,10 @@ static void scheduler_main(aes_server* S) {
             }
             if (slot.reqs.empty()) break;  // the budget is full: wait for completions
             slot.launch_s = S->now();
-            int rc = launch_slot(S, slot);
+            int rc = timed_cuda(S, [&] { return launch_slot(S, slot); });
             if (rc != AES_OK && !S->dryrun) cudaStreamSynchronize(slot.stream);  // staging may still be read
             {
-                SchedLock lk(S, S->stats_mu);
+                SchedLock lk(S, kLockStats);
                 S->stats.batches++;
                 S->stats.max_batch_msgs = std::max<uint64_t>(S->stats.max_batch_msgs, slot.reqs.size());
             }
@@ -457,13 +522,14 @@ static void scheduler_main(aes_server* S) {
                 slot.busy = true;
                 slot.bytes = bytes;
                 S->inflight_bytes += bytes;
-                SchedLock lk(S, S->stats_mu);
+                SchedLock lk(S, kLockStats);
                 S->stats.max_inflight_bytes = std::max<uint64_t>(S->stats.max_inflight_bytes, S->inflight_bytes);
             }
             worked = true;
         }
+        end_phase(S, kPhaseLaunch, &ph);  // (admission and launches)
         {
-            SchedLock lk(S, S->stats_mu);
+            SchedLock lk(S, kLockStats);
             S->stats.max_queue = std::max<uint64_t>(S->stats.max_queue, S->queue.size());
             publish_diagnostics(S);
         }
@@ -728,7 +794,9 @@ static void scheduler_resident(aes_server* S) {
     // Normally well before the kernel's own bound (80%); later in tests of the recovery.
     const double restart_s = 1e-5 * S->cfg.resident_restart_pct * S->cfg.resident_lifetime_ms;
     for (;;) {
+        double ph = S->now();
         bool worked = take_inbox(S);
+        end_phase(S, kPhaseInbox, &ph);
         // Completions: new entries of the completion queue, in order.  Ring
         // space is freed in publication order (a request's tiles and slot are
         // reused only once it and every request before it in its direction
@@ -764,23 +832,24 @@ static void scheduler_resident(aes_server* S) {
         }
         if (!finished.empty()) {  // one hand-over per pass, not one per request
             {
-                SchedLock lk(S, S->out_mu);
+                SchedLock lk(S, kLockDone);
                 S->done.insert(S->done.end(), finished.begin(), finished.end());
             }
             {
-                SchedLock lk(S, S->stats_mu);
+                SchedLock lk(S, kLockStats);
                 S->stats.completed += finished.size();
             }
             S->finished.fetch_add(finished.size());
             worked = true;
         }
+        end_phase(S, kPhaseDone, &ph);
         // Has the kernel ended?  (A driver query: on every pass while it is
         // stopping, else every 50 us -- it ends on its own only at its lifetime
         // bound or on a fault, and the query would lengthen every pass.)
         if (S->rlive && (S->rstopping || pass_s - last_query > 50e-6)) {
             last_query = pass_s;
             int err = AES_OK;
-            if (!resident_running(S, &err)) {
+            if (!timed_cuda(S, [&] { return resident_running(S, &err); })) {
                 S->rlive = false;
                 S->rstopping = false;
                 if (err == AES_OK) err = recover_resident(S);
@@ -797,6 +866,7 @@ static void scheduler_resident(aes_server* S) {
             __atomic_store_n(&S->rctrl->stop, 1u, __ATOMIC_RELEASE);
             S->rstopping = true;
         }
+        end_phase(S, kPhaseQuery, &ph);
         // Admission in arrival order while the budget and the ring have room.
         const double admit_s = S->now();
         size_t admitted = 0;
@@ -828,8 +898,9 @@ static void scheduler_resident(aes_server* S) {
             ++admitted;
             worked = true;
         }
+        end_phase(S, kPhaseAdmit, &ph);
         {
-            SchedLock lk(S, S->stats_mu);
+            SchedLock lk(S, kLockStats);
             if (admitted) {
                 S->stats.max_inflight_bytes = std::max<uint64_t>(S->stats.max_inflight_bytes, S->inflight_bytes);
                 S->stats.max_batch_msgs = 1;
@@ -839,9 +910,9 @@ static void scheduler_resident(aes_server* S) {
         }
         inflight = !S->rinflight[0].empty() || !S->rinflight[1].empty();
         if (inflight && !S->rlive) {  // published work and no kernel: (re)launch
-            const int rc = start_resident(S);
+            const int rc = timed_cuda(S, [&] { return start_resident(S); });
             {
-                SchedLock lk(S, S->stats_mu);
+                SchedLock lk(S, kLockStats);
                 S->stats.batches++;  // resident mode: kernel launches
             }
             if (rc == AES_OK)
@@ -850,6 +921,7 @@ static void scheduler_resident(aes_server* S) {
                 fail_resident_inflight(S, rc);
             worked = true;
         }
+        end_phase(S, kPhaseLaunch, &ph);
         if (worked) {
             last_work = S->now();
         } else {
@@ -900,8 +972,12 @@ static void push_inbox(aes_server* S, const Pending* p, size_t n) {
     }
     {
         std::lock_guard<std::mutex> lk(S->in_mu);
+        const double t = S->now();
         S->inbox.insert(S->inbox.end(), p, p + n);
         S->inbox_n.store(S->inbox.size(), std::memory_order_release);
+        const uint64_t held = (uint64_t)(1e9 * (S->now() - t));
+        if (held > S->submit_hold_ns.load(std::memory_order_relaxed))
+            S->submit_hold_ns.store(held, std::memory_order_relaxed);  // (submitters hold in_mu here)
     }
     S->in_cv.notify_one();
 }
@@ -925,8 +1001,18 @@ static void producer_main(aes_server* S) {
     ThreadWatch::usage(&cpu0, &inv_begin);
     inv_prev = inv_begin;
     uint64_t handovers = 0;
-    double late_max = 0;
+    double late_max = 0, late_at = 0, check_max = 0, check_at = 0;
     long late_invol = 0;
+    auto check = [&](const aes_server_request& r) {
+        const double t = S->now();
+        const int rc = check_request(S, r);
+        const double d = S->now() - t;
+        if (d > check_max) {
+            check_max = d;
+            check_at = t;
+        }
+        return rc;
+    };
     std::vector<Pending> due_now;
     const size_t n = S->replay_reqs.size();
     // Hands request r (already checked: rc) to the scheduler's batch, or
@@ -945,7 +1031,7 @@ static void producer_main(aes_server* S) {
         if (S->producer_stop.load()) break;
         // The next request is checked before its arrival time, so the driver
         // queries of the check are not part of its latency.
-        const int rc_first = check_request(S, S->replay_reqs[i]);
+        const int rc_first = check(S->replay_reqs[i]);
         const double due = start + S->replay_reqs[i].arrival_s;
         for (;;) {  // wait for the scheduled arrival time: sleep, then yield, then spin for the last 50 us
             const double wait = due - S->now();
@@ -963,7 +1049,7 @@ static void producer_main(aes_server* S) {
         take(S->replay_reqs[i++], rc_first);
         const double now = S->now();
         for (; i < n && start + S->replay_reqs[i].arrival_s <= now; ++i)
-            take(S->replay_reqs[i], check_request(S, S->replay_reqs[i]));
+            take(S->replay_reqs[i], check(S->replay_reqs[i]));
         push_inbox(S, due_now.data(), due_now.size());
         const double late = now - due;
         if (++handovers % 16 == 0 || late >= 20e-6) {
@@ -972,6 +1058,7 @@ static void producer_main(aes_server* S) {
             ThreadWatch::usage(&cpu, &inv);
             if (late > late_max) {
                 late_max = late;
+                late_at = due;
                 late_invol = inv - inv_prev;
             }
             inv_prev = inv;
@@ -982,12 +1069,18 @@ static void producer_main(aes_server* S) {
         long inv;
         ThreadWatch::usage(&cpu, &inv);
         std::lock_guard<std::mutex> lk(S->stats_mu);
-        if (late_max > 1e-9 * S->stats.producer_late_max_ns) {
-            S->stats.producer_late_max_ns = (uint64_t)(1e9 * late_max);
-            S->stats.producer_late_invol = (uint64_t)late_invol;
+        aes_server_diag& d = S->diag;
+        if (late_max > 1e-9 * d.producer_late_max_ns) {
+            d.producer_late_max_ns = (uint64_t)(1e9 * late_max);
+            d.producer_late_at_ns = (uint64_t)(1e9 * late_at);
+            d.producer_late_invol = (uint64_t)late_invol;
         }
-        S->stats.producer_invol += (uint64_t)(inv - inv_begin);
-        S->stats.producer_cpu = S->producer_cpu;
+        if (check_max > 1e-9 * d.producer_check_max_ns) {
+            d.producer_check_max_ns = (uint64_t)(1e9 * check_max);
+            d.producer_check_at_ns = (uint64_t)(1e9 * check_at);
+        }
+        d.producer_invol += (uint64_t)(inv - inv_begin);
+        d.producer_cpu = S->producer_cpu;
     }
     S->producer_running.store(false);
 }
@@ -1174,8 +1267,8 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
         return nullptr;
     }
     S->stats.budget_bytes = cfg.budget_bytes;
-    S->stats.sched_cpu = -1;
-    S->stats.producer_cpu = -1;
+    S->diag.sched_cpu = -1;
+    S->diag.producer_cpu = -1;
     S->t0 = std::chrono::steady_clock::now();
     S->magic = kServerMagic;
     S->scheduler = std::thread(S->resident ? scheduler_resident : scheduler_main, S);
@@ -1243,6 +1336,14 @@ int aes_server_get_stats(aes_server* S, aes_server_stats* out) {
     if (!out) return fail(AES_ERR_ARG, "out is NULL");
     std::lock_guard<std::mutex> lk(S->stats_mu);
     *out = S->stats;
+    return AES_OK;
+}
+
+int aes_server_get_diag(aes_server* S, aes_server_diag* out) {
+    if (!S || S->magic != kServerMagic) return fail(AES_ERR_ARG, "invalid aes_server");
+    if (!out) return fail(AES_ERR_ARG, "out is NULL");
+    std::lock_guard<std::mutex> lk(S->stats_mu);
+    *out = S->diag;
     return AES_OK;
 }
 

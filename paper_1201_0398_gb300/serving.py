@@ -18,7 +18,7 @@ GiB = 1 << 30
 def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8 << 30, nkeys: int = 1024,
         nstreams: int = 4, threads: int = 0, blocks_per_thread: int = 0, max_batch_msgs: int = 4096,
         pool_bytes: int = GiB, check_last: int = 1000, seed: int = workloads.SEED_SERVE,
-        resident: bool = False, pin_threads: bool = False) -> dict:
+        resident: bool = False, pin_threads: bool = False, poll_every_s: float = 0.0) -> dict:
     import torch
 
     w = workloads.serve_workload(rate=rate, duration_s=duration_s, nkeys=nkeys, seed=seed)
@@ -47,11 +47,34 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
     srv = Server(keys, budget_bytes=budget_bytes, nstreams=nstreams, threads=threads,
                  blocks_per_thread=blocks_per_thread, max_batch_msgs=max_batch_msgs, resident=resident,
                  pin_threads=pin_threads)
+    parts = []
+    polling = poll_every_s > 0
+    if polling:  # a client that takes its completions as they come (the server's queue stays short)
+        import threading
+        import time
+
+        stop = threading.Event()
+
+        def poller():
+            while not stop.is_set():
+                p = srv.poll(1 << 16)
+                if p.size:
+                    parts.append(p)
+                else:
+                    time.sleep(poll_every_s)
+
+        th = threading.Thread(target=poller)
+        th.start()
     srv.replay(reqs)
     srv.replay_join()
     srv.drain(120.0)
-    done = srv.poll_all()
+    if polling:
+        stop.set()
+        th.join()
+    parts.append(srv.poll_all())
+    done = np.concatenate(parts)
     stats = srv.stats()
+    diag = srv.diag()
     srv.close()
     ok = done["status"] == 0
     lat = (done["done_s"] - done["arrival_s"])[ok]
@@ -87,16 +110,31 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
         "budget_bytes": int(budget_bytes), "nstreams": nstreams, "shape": f"{threads or 512}x{blocks_per_thread or (2 if resident else 1)}",
         "checked_alone": int(len(idx)), "mismatches": mismatches,
         "host_threads": {
-            "pinned_cpus": [int(stats["sched_cpu"]), int(stats["producer_cpu"])],
-            "sched_passes": int(stats["sched_passes"]),
-            "sched_worst_window_us": stats["sched_worst_window_ns"] / 1e3,
-            "sched_worst_window_cpu_us": stats["sched_worst_window_cpu_ns"] / 1e3,
-            "sched_worst_window_invol": int(stats["sched_worst_window_invol"]),
-            "sched_invol": int(stats["sched_invol"]),
-            "sched_lock_wait_max_us": stats["sched_lock_wait_max_ns"] / 1e3,
-            "producer_late_max_us": stats["producer_late_max_ns"] / 1e3,
-            "producer_late_invol": int(stats["producer_late_invol"]),
-            "producer_invol": int(stats["producer_invol"])},
+            "pinned_cpus": [int(diag["sched_cpu"]), int(diag["producer_cpu"])],
+            "sched_passes": int(diag["sched_passes"]),
+            "sched_worst_window_us": diag["sched_worst_window_ns"] / 1e3,
+            "sched_worst_window_cpu_us": diag["sched_worst_window_cpu_ns"] / 1e3,
+            "sched_worst_window_invol": int(diag["sched_worst_window_invol"]),
+            "sched_worst_window_vol": int(diag["sched_worst_window_vol"]),
+            "sched_worst_window_faults": [int(diag["sched_worst_window_minflt"]),
+                                          int(diag["sched_worst_window_majflt"])],
+            "sched_worst_window_at_s": diag["sched_worst_window_at_ns"] / 1e9,
+            "sched_invol": int(diag["sched_invol"]),
+            "lock_wait_max_us": {k: v / 1e3 for k, v in zip(("inbox", "done", "stats"), diag["lock_wait_max_ns"])},
+            "lock_wait_at_s": {k: v / 1e9 for k, v in zip(("inbox", "done", "stats"), diag["lock_wait_at_ns"])},
+            "cuda_call_max_us": diag["cuda_call_max_ns"] / 1e3,
+            "cuda_call_at_s": diag["cuda_call_at_ns"] / 1e9,
+            "sched_phase_max_us": {k: v / 1e3 for k, v in zip(("inbox", "done", "query", "admit", "launch"),
+                                                              diag["sched_phase_max_ns"])},
+            "sched_phase_at_s": {k: v / 1e9 for k, v in zip(("inbox", "done", "query", "admit", "launch"),
+                                                             diag["sched_phase_at_ns"])},
+            "inbox_hold_max_us": [v / 1e3 for v in diag["inbox_hold_max_ns"]],
+            "producer_late_max_us": diag["producer_late_max_ns"] / 1e3,
+            "producer_late_at_s": diag["producer_late_at_ns"] / 1e9,
+            "producer_late_invol": int(diag["producer_late_invol"]),
+            "producer_invol": int(diag["producer_invol"]),
+            "producer_check_max_us": diag["producer_check_max_ns"] / 1e3,
+            "producer_check_at_s": diag["producer_check_at_ns"] / 1e9},
         "workload": f"Poisson {rate:.0f} req/s for {duration_s:g} s, sizes log-uniform 64 B-1 MiB (x16 B), "
                     f"{nkeys} resident keys (128/192/256), encrypt/decrypt 50/50, {budget_bytes >> 30} GiB budget",
     }
