@@ -348,7 +348,8 @@ typedef struct aes_server_diag {
     uint64_t producer_late_at_ns;
     uint64_t producer_late_invol;       /* replay: involuntary switches since the thread's reading before that */
     uint64_t producer_invol;            /* replay: involuntary context switches over all replays */
-    uint64_t producer_check_max_ns;     /* replay: longest host check of one request (driver pointer queries) */
+    uint64_t producer_check_max_ns;     /* replay: longest host check of one request (driver pointer queries),
+                                           made when aes_server_replay is called */
     uint64_t producer_check_at_ns;
     int64_t sched_cpu;                  /* CPU the scheduler thread is pinned to (AES_SERVER_PIN_THREADS), else -1 */
     int64_t producer_cpu;               /* CPU the replay thread is pinned to, else -1 */
@@ -369,7 +370,10 @@ int aes_server_submit(aes_server* server, const aes_server_request* req);
 
 /* Starts a producer thread that submits reqs[i] at arrival_s[i] seconds after
  * the call (open loop: late submissions keep their scheduled arrival time, so
- * queueing delay is counted).  The array is copied.  One replay at a time. */
+ * queueing delay is counted).  The array is copied and every request is
+ * checked during this call (the caller must keep its buffers valid until the
+ * requests complete); a request that fails its check completes with its error
+ * at its arrival time.  One replay at a time. */
 int aes_server_replay(aes_server* server, const aes_server_request* reqs, size_t n);
 
 /* Waits for the replay thread (stop_early != 0: ends it after its current request). */

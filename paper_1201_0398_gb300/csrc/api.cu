@@ -190,7 +190,8 @@ static PointerAttrsFn pointer_attrs_fn() {
 // Unregistered pageable host memory is refused even where the GPU could read
 // it, because its extent cannot be checked before the launch.  One driver call
 // reads the memory type, the managed flag, the device address and the extent.
-int check_device_range(const void* p, size_t bytes, const char* what) {
+static int check_device_range_ex(const void* p, size_t bytes, const char* what, uintptr_t* alloc_lo,
+                                 uintptr_t* alloc_hi) {
     if (!p) return fail(AES_ERR_ARG, "%s is NULL", what);
     if (((uintptr_t)p & 15u) != 0) return fail(AES_ERR_ALIGN, "%s (%p) is not 16-byte aligned", what, p);
     PointerAttrsFn get = pointer_attrs_fn();
@@ -215,7 +216,30 @@ int check_device_range(const void* p, size_t bytes, const char* what) {
     if (lo < (uintptr_t)start || lo > end || bytes > end - lo)
         return fail(AES_ERR_ARG, "%s: %zu bytes at %p run past the end of its allocation (%zu bytes left)", what,
                     bytes, p, lo <= end ? (size_t)(end - lo) : (size_t)0);
+    *alloc_lo = (uintptr_t)start;
+    *alloc_hi = end;
     return AES_OK;
+}
+
+int check_device_range(const void* p, size_t bytes, const char* what) {
+    uintptr_t lo = 0, hi = 0;
+    return check_device_range_ex(p, bytes, what, &lo, &hi);
+}
+
+int check_device_range_cached(const void* p, size_t bytes, const char* what, RangeCache* cache) {
+    if (!cache) return check_device_range(p, bytes, what);
+    const uintptr_t a = (uintptr_t)p;
+    if (p && (a & 15u) == 0)
+        for (int i = 0; i < cache->n; ++i)
+            if (a >= cache->lo[i] && a <= cache->hi[i] && bytes <= cache->hi[i] - a) return AES_OK;
+    uintptr_t lo = 0, hi = 0;
+    const int rc = check_device_range_ex(p, bytes, what, &lo, &hi);
+    if (rc == AES_OK) {  // remember the allocation (the oldest entry makes room)
+        const int k = cache->n < RangeCache::kSize ? cache->n++ : (cache->next++ % RangeCache::kSize);
+        cache->lo[k] = lo;
+        cache->hi[k] = hi;
+    }
+    return rc;
 }
 
 // ------------------------------------------------------- launch defaults

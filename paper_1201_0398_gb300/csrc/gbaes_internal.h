@@ -62,6 +62,19 @@ int set_max_dynamic_smem(const void* fn, int bytes);
 // Checks that [p, p+bytes) is 16-byte aligned device-reachable memory.
 int check_device_range(const void* p, size_t bytes, const char* what);
 
+// Allocations already found valid during one pass of checks over many ranges
+// (which must not free or replace them meanwhile): a range inside one of them
+// needs no driver query.
+struct RangeCache {
+    static constexpr int kSize = 8;
+    uintptr_t lo[kSize] = {}, hi[kSize] = {};
+    int n = 0;
+    unsigned next = 0;
+};
+
+// check_device_range through a cache (nullptr: no cache).
+int check_device_range_cached(const void* p, size_t bytes, const char* what, RangeCache* cache);
+
 // Largest call (in blocks) that AES_KERNEL_TABLE runs with compact tables.
 uint64_t compact_limit_blocks(int sms);
 

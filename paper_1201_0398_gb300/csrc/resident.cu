@@ -370,7 +370,12 @@ __device__ __forceinline__ void completer_lane(const ResArgs& a, uint32_t ctl, c
     for (uint32_t i = 0;; ++i) {
         const uint32_t k = i & 1u, par = (i >> 1) & 1u, sl = ctl + kSlotBytes * k;
         if (!mbar_wait(mb.full + 8u * k, par, deadline)) break;
-        if (lds(sl + 48u)) return;
+        if (lds(sl + 48u)) {
+            // Every tile this CTA was handed is counted: mark its exit in page-locked
+            // memory, so that the host sees the kernel end without asking the driver.
+            st_release_sys(a.exit_gen + blockIdx.x, a.gen);
+            return;
+        }
         if (!mbar_wait(mb.empty + 8u * k, par, deadline)) break;
         account_tile(a, sl);
         mbar_arrive(mb.free_ + 8u * k);

@@ -78,7 +78,11 @@ struct ResArgs {
     uint32_t cq_size;               // power of two, 2 * ring_items (requests in flight, both directions)
     uint32_t cq_log2;               // log2(cq_size)
     uint64_t lifetime_ns;           // a CTA leaves once this long has passed since its start
+    uint64_t* exit_gen;             // [grid] device view of page-locked memory: gen once a CTA has left normally
+    uint64_t gen;                   // this launch's number (from 1)
 };
+
+constexpr uint32_t kResidentMaxCtas = 1024;  // exit words in the ring memory (one per CTA)
 
 // Compute threads per CTA of the resident kernel (at most; two control warps come on top).
 constexpr uint32_t kResidentMaxThreads = 512;

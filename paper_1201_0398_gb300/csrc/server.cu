@@ -190,6 +190,7 @@ struct aes_server {
     std::thread scheduler;
     std::thread producer;
     std::vector<aes_server_request> replay_reqs;
+    std::vector<int32_t> replay_rc;  // each replayed request's check, made when the replay starts
     double replay_start = 0;
 
     // Resident mode (scheduler thread only, except where noted).
@@ -211,6 +212,11 @@ struct aes_server {
     std::deque<ResItem> rinflight[2];
     bool rlive = false;               // a kernel (or its dry-run stand-in) is running
     bool rstopping = false;           // its stop word is set: nothing is published until it has ended
+    double rstop_s = 0;               // when the stop word was set
+    double rprogress_s = 0;           // last publication or completion
+    uint64_t rgen = 0;                // launches so far (the running kernel's number)
+    uint32_t rgrid = 0;               // its CTAs
+    uint64_t* rexit = nullptr;        // host view of the CTAs' exit words
     double rlaunch_s = 0;             // its launch
     // Dry run: one host thread runs the kernel's ticket/record/count/status protocol.
     std::vector<uint64_t> fake_claim, fake_done;  // stand-in thread, or the scheduler while none runs
@@ -632,14 +638,26 @@ static int start_resident(aes_server* S) {
         S->fake = std::thread(fake_kernel_main, S);
         return AES_OK;
     }
+    S->rargs.gen = ++S->rgen;
     return launch_resident(S->rargs, S->cfg.threads, S->cfg.blocks_per_thread, S->rstream);
 }
 
 // True while the kernel runs; AES_ERR_CUDA in *err if it failed.
-static bool resident_running(aes_server* S, int* err) {
+// True while the kernel runs; AES_ERR_CUDA in *err if it failed.  While its
+// CTAs keep working this makes no CUDA call: each CTA marks its normal exit in
+// page-locked memory, and the stream is asked only to confirm an end that every
+// CTA has marked, or when the kernel shows no sign of life (`suspect`: nothing
+// published or completed for 50 ms with work in flight, or 50 ms after the stop
+// word), which is how a fault shows.  (Asked every 50 us, the stream query now
+// and then waited tens of milliseconds inside the driver, and every request in
+// flight waited with it.)
+static bool resident_running(aes_server* S, int* err, bool suspect) {
     *err = AES_OK;
     if (S->dryrun) return S->fake_running.load(std::memory_order_acquire);
-    const cudaError_t q = cudaStreamQuery(S->rstream);
+    bool all = true;
+    for (uint32_t i = 0; i < S->rgrid && all; ++i) all = __atomic_load_n(&S->rexit[i], __ATOMIC_ACQUIRE) == S->rgen;
+    if (!all && !suspect) return true;
+    const cudaError_t q = timed_cuda(S, [&] { return cudaStreamQuery(S->rstream); });
     if (q == cudaErrorNotReady) return true;
     if (q != cudaSuccess) *err = fail(AES_ERR_CUDA, "resident kernel: %s", cudaGetErrorString(q));
     return false;
@@ -821,6 +839,7 @@ static void scheduler_resident(aes_server* S) {
             S->inflight_bytes -= it.bytes;
             S->rtiles_open -= it.ntiles;
             finished.push_back(aes_server_completion{it.p.r.id, AES_OK, 1, it.p.arrival, it.launch_s, pass_s});
+            S->rprogress_s = pass_s;
         }
         for (int d = 0; d < 2; ++d) {
             while (!S->rinflight[d].empty() && S->rinflight[d].front().done) {
@@ -843,13 +862,15 @@ static void scheduler_resident(aes_server* S) {
             worked = true;
         }
         end_phase(S, kPhaseDone, &ph);
-        // Has the kernel ended?  (A driver query: on every pass while it is
-        // stopping, else every 50 us -- it ends on its own only at its lifetime
-        // bound or on a fault, and the query would lengthen every pass.)
+        // Has the kernel ended?  (Its CTAs' exit words: on every pass while it
+        // is stopping, else every 50 us -- it ends on its own only at its
+        // lifetime bound or on a fault.)
         if (S->rlive && (S->rstopping || pass_s - last_query > 50e-6)) {
             last_query = pass_s;
             int err = AES_OK;
-            if (!timed_cuda(S, [&] { return resident_running(S, &err); })) {
+            const bool busy = !S->rinflight[0].empty() || !S->rinflight[1].empty();
+            const bool suspect = (busy && pass_s - S->rprogress_s > 0.05) || (S->rstopping && pass_s - S->rstop_s > 0.05);
+            if (!resident_running(S, &err, suspect)) {
                 S->rlive = false;
                 S->rstopping = false;
                 if (err == AES_OK) err = recover_resident(S);
@@ -865,6 +886,7 @@ static void scheduler_resident(aes_server* S) {
             ((quiet && (S->now() - last_work > idle_s || S->stop.load())) || S->now() - S->rlaunch_s > restart_s)) {
             __atomic_store_n(&S->rctrl->stop, 1u, __ATOMIC_RELEASE);
             S->rstopping = true;
+            S->rstop_s = S->now();
         }
         end_phase(S, kPhaseQuery, &ph);
         // Admission in arrival order while the budget and the ring have room.
@@ -892,6 +914,7 @@ static void scheduler_resident(aes_server* S) {
                 continue;
             }
             if (!publish(S, p, b, admit_s)) break;
+            S->rprogress_s = admit_s;
             ++S->batch_counter;
             S->inflight_bytes += b;
             S->queue.pop_front();
@@ -915,10 +938,12 @@ static void scheduler_resident(aes_server* S) {
                 SchedLock lk(S, kLockStats);
                 S->stats.batches++;  // resident mode: kernel launches
             }
-            if (rc == AES_OK)
+            if (rc == AES_OK) {
                 S->rlive = true;
-            else
+                S->rprogress_s = S->now();
+            } else {
                 fail_resident_inflight(S, rc);
+            }
             worked = true;
         }
         end_phase(S, kPhaseLaunch, &ph);
@@ -937,7 +962,7 @@ static void scheduler_resident(aes_server* S) {
 }
 
 // Checks one request on the host (sizes, key, pointers); AES_OK or the error it is refused with.
-static int check_request(aes_server* S, const aes_server_request& r) {
+static int check_request(aes_server* S, const aes_server_request& r, RangeCache* cache = nullptr) {
     if (r.key_index >= S->keys.size())
         return fail(AES_ERR_ARG, "request %llu: key_index %u >= %zu", (unsigned long long)r.id, r.key_index,
                     S->keys.size());
@@ -951,8 +976,8 @@ static int check_request(aes_server* S, const aes_server_request& r) {
     }
     if (!S->dryrun && r.nblocks) {
         const size_t bytes = (size_t)r.nblocks * 16;
-        int rc = check_device_range(r.in, bytes, "request in");
-        if (!rc) rc = check_device_range(r.out, bytes, "request out");
+        int rc = check_device_range_cached(r.in, bytes, "request in", cache);
+        if (!rc) rc = check_device_range_cached(r.out, bytes, "request out", cache);
         if (rc) return rc;
         const uintptr_t i0 = (uintptr_t)r.in, o0 = (uintptr_t)r.out;
         if (i0 != o0 && i0 < o0 + bytes && o0 < i0 + bytes) return fail(AES_ERR_ARG, "request in/out overlap partially");
@@ -1001,18 +1026,10 @@ static void producer_main(aes_server* S) {
     ThreadWatch::usage(&cpu0, &inv_begin);
     inv_prev = inv_begin;
     uint64_t handovers = 0;
-    double late_max = 0, late_at = 0, check_max = 0, check_at = 0;
+    double late_max = 0, late_at = 0;
     long late_invol = 0;
-    auto check = [&](const aes_server_request& r) {
-        const double t = S->now();
-        const int rc = check_request(S, r);
-        const double d = S->now() - t;
-        if (d > check_max) {
-            check_max = d;
-            check_at = t;
-        }
-        return rc;
-    };
+    // Every request was checked when the replay was started (no driver call here).
+    auto check = [&](size_t i) { return S->replay_rc[i]; };
     std::vector<Pending> due_now;
     const size_t n = S->replay_reqs.size();
     // Hands request r (already checked: rc) to the scheduler's batch, or
@@ -1031,7 +1048,7 @@ static void producer_main(aes_server* S) {
         if (S->producer_stop.load()) break;
         // The next request is checked before its arrival time, so the driver
         // queries of the check are not part of its latency.
-        const int rc_first = check(S->replay_reqs[i]);
+        const int rc_first = check(i);
         const double due = start + S->replay_reqs[i].arrival_s;
         for (;;) {  // wait for the scheduled arrival time: sleep, then yield, then spin for the last 50 us
             const double wait = due - S->now();
@@ -1049,7 +1066,7 @@ static void producer_main(aes_server* S) {
         take(S->replay_reqs[i++], rc_first);
         const double now = S->now();
         for (; i < n && start + S->replay_reqs[i].arrival_s <= now; ++i)
-            take(S->replay_reqs[i], check(S->replay_reqs[i]));
+            take(S->replay_reqs[i], check(i));
         push_inbox(S, due_now.data(), due_now.size());
         const double late = now - due;
         if (++handovers % 16 == 0 || late >= 20e-6) {
@@ -1074,10 +1091,6 @@ static void producer_main(aes_server* S) {
             d.producer_late_max_ns = (uint64_t)(1e9 * late_max);
             d.producer_late_at_ns = (uint64_t)(1e9 * late_at);
             d.producer_late_invol = (uint64_t)late_invol;
-        }
-        if (check_max > 1e-9 * d.producer_check_max_ns) {
-            d.producer_check_max_ns = (uint64_t)(1e9 * check_max);
-            d.producer_check_at_ns = (uint64_t)(1e9 * check_at);
         }
         d.producer_invol += (uint64_t)(inv - inv_begin);
         d.producer_cpu = S->producer_cpu;
@@ -1119,7 +1132,8 @@ static int setup_resident(aes_server* S) {
     const aes_server_config& c = S->cfg;
     const uint32_t rt = c.ring_tiles, ri = c.ring_items;
     const uint32_t cq = 2 * ri;  // no more requests than this are in flight
-    const size_t bytes = sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt + sizeof(ResDone) * (size_t)cq;
+    const size_t exit_off = sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt + sizeof(ResDone) * (size_t)cq;
+    const size_t bytes = exit_off + sizeof(uint64_t) * kResidentMaxCtas;
     uint8_t* dev_view = nullptr;
     if (S->dryrun) {
         S->ring_mem = (uint8_t*)aligned_alloc(64, (bytes + 63) & ~(size_t)63);
@@ -1156,6 +1170,8 @@ static int setup_resident(aes_server* S) {
     S->rargs.ctrl = (const ResCtrl*)dev_view;
     S->rargs.tiles = (const ResTile*)(dev_view + sizeof(ResCtrl));
     S->rargs.cq = (ResDone*)(dev_view + sizeof(ResCtrl) + sizeof(ResTile) * 2 * (size_t)rt);
+    S->rexit = (uint64_t*)(S->ring_mem + exit_off);
+    S->rargs.exit_gen = (uint64_t*)(dev_view + exit_off);
     S->rargs.cq_size = cq;
     S->rargs.cq_log2 = (uint32_t)__builtin_ctz(cq);
     S->rargs.keys = S->dev_keys;
@@ -1166,7 +1182,9 @@ static int setup_resident(aes_server* S) {
         DeviceInfo info;
         int rc = current_device_info(&info);
         if (rc) return rc;
+        if ((uint32_t)info.sms > kResidentMaxCtas) return fail(AES_ERR_CUDA, "more SMs than resident CTAs supported");
         S->spread = (uint32_t)info.sms;
+        S->rgrid = (uint32_t)info.sms;
     } else {
         S->spread = 8;
     }
@@ -1297,6 +1315,30 @@ int aes_server_replay(aes_server* S, const aes_server_request* reqs, size_t n) {
     for (size_t i = 1; i < n; ++i)
         if (reqs[i].arrival_s < reqs[i - 1].arrival_s) return fail(AES_ERR_ARG, "arrival times must not decrease");
     S->replay_reqs.assign(reqs, reqs + n);
+    // Checks every request now, not on the replay thread: its hand-overs then
+    // make no driver call (a pointer query can wait behind the driver for tens of
+    // milliseconds).  The caller keeps the buffers valid for the replay, so the
+    // allocations found valid here stay valid, and a cache of them spares the
+    // driver a query per request.
+    S->replay_rc.resize(n);
+    RangeCache cache;
+    double check_max = 0, check_at = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const double t = S->now();
+        S->replay_rc[i] = check_request(S, reqs[i], &cache);
+        if (S->now() - t > check_max) {
+            check_max = S->now() - t;
+            check_at = t;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->stats_mu);
+        if (check_max > 1e-9 * S->diag.producer_check_max_ns) {
+            S->diag.producer_check_max_ns = (uint64_t)(1e9 * check_max);
+            S->diag.producer_check_at_ns = (uint64_t)(1e9 * check_at);
+        }
+    }
+    clear_error();
     S->producer_stop.store(false);
     S->producer_running.store(true);
     S->producer = std::thread(producer_main, S);
