@@ -473,9 +473,11 @@ def run_ours(args):
         from paper_1201_0398_gb300 import serving as serving_mod
 
         seed = dist.shard_seed(workloads.SEED_SERVE, ranks)
-        serving = serving_mod.run(duration_s=args.serve_seconds, seed=seed, resident=True)
+        # The client takes its completions every 2 ms while requests run, as a serving client would.
+        serving = serving_mod.run(duration_s=args.serve_seconds, seed=seed, resident=True, poll_every_s=0.002)
         torch.cuda.empty_cache()
-        serving["launch_per_batch"] = {k: v for k, v in serving_mod.run(duration_s=args.serve_seconds, seed=seed).items()
+        serving["launch_per_batch"] = {k: v for k, v in serving_mod.run(duration_s=args.serve_seconds, seed=seed,
+                                                                         poll_every_s=0.002).items()
                                        if k != "workload"}
         torch.cuda.empty_cache()
 
@@ -791,7 +793,8 @@ def run_serve_sweep(args):
             torch.cuda.empty_cache()
             keep = ("mode", "value", "offered_gbs", "requests", "completed_ok", "p50_ms", "p99_ms", "p999_ms",
                     "max_ms", "p50_queue_ms", "p50_service_ms", "max_queue", "max_inflight_bytes", "shape",
-                    "mismatches", "mean_batch_msgs", "p50_service_ms", "p99_service_ms", "host_threads")
+                    "mismatches", "mean_batch_msgs", "p50_service_ms", "p99_service_ms", "host_threads",
+                    "kernel_launches")
             print(json.dumps({"sweep": "serving", "rate": rate, "seconds": args.serve_sweep_seconds,
                               **{k: r[k] for k in keep if k in r}}), flush=True)
 

@@ -338,6 +338,8 @@ typedef struct aes_server_diag {
     uint64_t lock_wait_at_ns[3];
     uint64_t cuda_call_max_ns;          /* the scheduler's longest CUDA call (event or stream query, launch) */
     uint64_t cuda_call_at_ns;
+    uint64_t stream_queries[2];         /* resident mode: stream queries made to confirm an end every CTA had
+                                           marked, and because the kernel showed no sign of life for 50 ms */
     uint64_t sched_phase_max_ns[5];     /* the scheduler's longest pass phase: taking submissions, completions,
                                            kernel or event queries, admission, launches and statistics (in
                                            launch-per-batch mode, completions count under the queries and

@@ -476,6 +476,7 @@ class _ServerDiag(ctypes.Structure):
                                                 "sched_worst_window_majflt", "sched_invol")] +
                 [("lock_wait_max_ns", ctypes.c_uint64 * 3), ("lock_wait_at_ns", ctypes.c_uint64 * 3)] +
                 [(n, ctypes.c_uint64) for n in ("cuda_call_max_ns", "cuda_call_at_ns")] +
+                [("stream_queries", ctypes.c_uint64 * 2)] +
                 [("sched_phase_max_ns", ctypes.c_uint64 * 5), ("sched_phase_at_ns", ctypes.c_uint64 * 5),
                  ("inbox_hold_max_ns", ctypes.c_uint64 * 2)] +
                 [(n, ctypes.c_uint64) for n in ("producer_late_max_ns", "producer_late_at_ns", "producer_late_invol",
@@ -522,8 +523,12 @@ class Server:
     def drain(self, timeout_s: float = -1.0):
         _check(self._lib.aes_server_drain(self._h, float(timeout_s)))
 
-    def poll(self, max_items: int = 1 << 22) -> np.ndarray:
-        out = np.zeros(max_items, COMPLETION)
+    def poll(self, max_items: int = 1 << 22, out: np.ndarray | None = None) -> np.ndarray:
+        """Up to max_items completions (into `out`, a COMPLETION array, if given: a buffer reused across
+        polls spares the server's lock a copy into fresh memory)."""
+        if out is None:
+            out = np.zeros(max_items, COMPLETION)
+        max_items = min(max_items, out.size)
         n = _check(self._lib.aes_server_poll(self._h, ctypes.c_void_p(out.ctypes.data), max_items))
         return out[:n]
 

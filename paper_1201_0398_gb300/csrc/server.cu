@@ -230,6 +230,7 @@ struct aes_server {
     ThreadWatch sched_watch;
     double lock_wait_max[3] = {0, 0, 0}, lock_wait_at[3] = {0, 0, 0};  // submissions, completions, stats
     double cuda_call_max = 0, cuda_call_at = 0;
+    uint64_t stream_queries[2] = {0, 0};  // resident: to confirm an end, for lack of progress
     double phase_max[5] = {0, 0, 0, 0, 0}, phase_at[5] = {0, 0, 0, 0, 0};  // scheduler pass phases
     double inbox_hold_max = 0;                 // by the scheduler
     std::atomic<uint64_t> submit_hold_ns{0};   // by a submitter (replay thread or aes_server_submit)
@@ -331,6 +332,8 @@ static void publish_diagnostics(aes_server* S) {
     }
     d.cuda_call_max_ns = (uint64_t)(1e9 * S->cuda_call_max);
     d.cuda_call_at_ns = (uint64_t)(1e9 * S->cuda_call_at);
+    d.stream_queries[0] = S->stream_queries[0];
+    d.stream_queries[1] = S->stream_queries[1];
     for (int i = 0; i < 5; ++i) {
         d.sched_phase_max_ns[i] = (uint64_t)(1e9 * S->phase_max[i]);
         d.sched_phase_at_ns[i] = (uint64_t)(1e9 * S->phase_at[i]);
@@ -657,6 +660,7 @@ static bool resident_running(aes_server* S, int* err, bool suspect) {
     bool all = true;
     for (uint32_t i = 0; i < S->rgrid && all; ++i) all = __atomic_load_n(&S->rexit[i], __ATOMIC_ACQUIRE) == S->rgen;
     if (!all && !suspect) return true;
+    ++S->stream_queries[all ? 0 : 1];
     const cudaError_t q = timed_cuda(S, [&] { return cudaStreamQuery(S->rstream); });
     if (q == cudaErrorNotReady) return true;
     if (q != cudaSuccess) *err = fail(AES_ERR_CUDA, "resident kernel: %s", cudaGetErrorString(q));

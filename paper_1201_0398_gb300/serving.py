@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import REQUEST, Key, Server, ecb_ex, workloads
+from . import COMPLETION, REQUEST, Key, Server, ecb_ex, workloads
 
 GiB = 1 << 30
 
@@ -55,11 +55,13 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
 
         stop = threading.Event()
 
+        buf = np.zeros(1 << 16, COMPLETION)  # reused: the copy under the server's lock lands in touched memory
+
         def poller():
             while not stop.is_set():
-                p = srv.poll(1 << 16)
+                p = srv.poll(buf.size, out=buf)
                 if p.size:
-                    parts.append(p)
+                    parts.append(p.copy())
                 else:
                     time.sleep(poll_every_s)
 
@@ -124,6 +126,8 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
             "lock_wait_at_s": {k: v / 1e9 for k, v in zip(("inbox", "done", "stats"), diag["lock_wait_at_ns"])},
             "cuda_call_max_us": diag["cuda_call_max_ns"] / 1e3,
             "cuda_call_at_s": diag["cuda_call_at_ns"] / 1e9,
+            "stream_queries": {"confirm_end": int(diag["stream_queries"][0]),
+                               "no_progress": int(diag["stream_queries"][1])},
             "sched_phase_max_us": {k: v / 1e3 for k, v in zip(("inbox", "done", "query", "admit", "launch"),
                                                               diag["sched_phase_max_ns"])},
             "sched_phase_at_s": {k: v / 1e9 for k, v in zip(("inbox", "done", "query", "admit", "launch"),
