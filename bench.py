@@ -473,11 +473,9 @@ def run_ours(args):
         from paper_1201_0398_gb300 import serving as serving_mod
 
         seed = dist.shard_seed(workloads.SEED_SERVE, ranks)
-        # The client takes its completions every 2 ms while requests run, as a serving client would.
-        serving = serving_mod.run(duration_s=args.serve_seconds, seed=seed, resident=True, poll_every_s=0.002)
+        serving = serving_mod.run(duration_s=args.serve_seconds, seed=seed, resident=True)
         torch.cuda.empty_cache()
-        serving["launch_per_batch"] = {k: v for k, v in serving_mod.run(duration_s=args.serve_seconds, seed=seed,
-                                                                         poll_every_s=0.002).items()
+        serving["launch_per_batch"] = {k: v for k, v in serving_mod.run(duration_s=args.serve_seconds, seed=seed).items()
                                        if k != "workload"}
         torch.cuda.empty_cache()
 
