@@ -203,22 +203,36 @@ int aes_ecb_batch_noalloc(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* 
 
 /* ------------------------------------------------------- host pipeline
  * ECB on data in host memory (Section 3 copies every texture over the bus and
- * Fig. 3 shows those copies dominating small inputs).  A pipeline owns `depth`
- * device staging slots of chunk_bytes each (0, 0 = 64 MiB x 4), each with its
- * own stream; chunks go round-robin over the slots (copy in, in-place table
- * kernel, copy out), so copies in both directions overlap the kernels. */
+ * Fig. 3 shows those copies dominating small inputs).  A pipeline picks how the
+ * data reaches the SMs:
+ *  - AES_PIPE_STAGED: `depth` device staging slots of chunk_bytes each (0, 0 =
+ *    64 MiB x 4), each with its own stream; chunks go round-robin over the
+ *    slots (copy in, in-place table kernel, copy out), so copies in both
+ *    directions overlap the kernels.
+ *  - AES_PIPE_DIRECT: no staging; one table-kernel launch reads the host input
+ *    and writes the host output over the host link (on a coherent link such as
+ *    NVLink-C2C the faster of the two).  chunk_bytes and depth are checked but
+ *    not used. */
+#define AES_PIPE_STAGED 0
+#define AES_PIPE_DIRECT 1
 typedef struct aes_pipeline aes_pipeline;
 
-/* Allocates the staging slots on the current device (cudaMalloc).  chunk_bytes:
- * multiple of 16; depth: 1..16.  NULL on error. */
+/* Creates a pipeline on the current device; staged mode allocates its slots
+ * (cudaMalloc) and streams.  chunk_bytes: multiple of 16; depth: 1..16; mode:
+ * AES_PIPE_STAGED or AES_PIPE_DIRECT.  NULL on error (AES_ERR_ARG for a bad
+ * argument, before any CUDA call). */
+aes_pipeline* aes_pipeline_create_ex(size_t chunk_bytes, int depth, int mode);
+
+/* aes_pipeline_create_ex(chunk_bytes, depth, AES_PIPE_STAGED). */
 aes_pipeline* aes_pipeline_create(size_t chunk_bytes, int depth);
 
 /* ECB over nblocks blocks from host_in to host_out: page-locked host memory
  * (cudaHostAlloc / cudaHostRegister; device memory also works), each covering
  * 16*nblocks bytes (AES_ERR_ARG otherwise); host_in == host_out allowed.
- * Asynchronous on `stream`: the stream waits for every chunk's copy-out, so
- * host_out is complete once the stream is.  One pipeline serves one call at a
- * time (calls from several threads serialise on it). */
+ * Asynchronous on `stream`: the stream waits for every chunk's copy-out (staged)
+ * or for the kernel (direct), so host_out is complete once the stream is.  One
+ * staged pipeline serves one call at a time (calls from several threads
+ * serialise on it); a direct pipeline holds no state between calls. */
 int aes_pipeline_ecb(aes_pipeline* pipe, const aes_ctx* ctx, int decrypt, const void* host_in, void* host_out,
                      size_t nblocks, void* stream);
 

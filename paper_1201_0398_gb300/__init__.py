@@ -52,6 +52,8 @@ __all__ = [
     "KERNEL_TABLE_REPLICATED",
     "CTR_BE128",
     "CTR_LE32_CARRY",
+    "PIPE_STAGED",
+    "PIPE_DIRECT",
 ]
 
 KERNEL_TABLE = 0
@@ -60,6 +62,8 @@ KERNEL_TABLE_COMPACT = 2
 KERNEL_TABLE_REPLICATED = 3
 CTR_BE128 = 0
 CTR_LE32_CARRY = 1
+PIPE_STAGED = 0
+PIPE_DIRECT = 1
 
 ERRORS = {
     -1: "AES_ERR_ARG",
@@ -116,6 +120,7 @@ def _declare(lib):
         "aes_batch_tiles": (c.c_int, [vp, sz, vp, sz, c.c_int, u32p, sz]),
         "aes_ecb_batch_noalloc": (c.c_int, [vp, sz, vp, sz, vp, sz, vp, sz, vp]),
         "aes_pipeline_create": (vp, [sz, c.c_int]),
+        "aes_pipeline_create_ex": (vp, [sz, c.c_int, c.c_int]),
         "aes_pipeline_ecb": (c.c_int, [vp, vp, c.c_int, vp, vp, sz, vp]),
         "aes_pipeline_free": (None, [vp]),
         "aes_server_create": (vp, [vp, sz, vp]),
@@ -413,11 +418,13 @@ def batch_tiles(descs: np.ndarray, keys, tile_blocks: int) -> np.ndarray:
 
 
 class Pipeline:
-    """ECB on page-locked host buffers through device staging slots (aes_pipeline)."""
+    """ECB on page-locked host buffers (aes_pipeline): through device staging
+    slots and copy engines (mode PIPE_STAGED), or with the kernel reading and
+    writing the host buffers over the host link (PIPE_DIRECT)."""
 
-    def __init__(self, chunk_bytes: int = 64 << 20, depth: int = 4):
+    def __init__(self, chunk_bytes: int = 64 << 20, depth: int = 4, mode: int = 0):
         self._lib = load()
-        h = self._lib.aes_pipeline_create(int(chunk_bytes), int(depth))
+        h = self._lib.aes_pipeline_create_ex(int(chunk_bytes), int(depth), int(mode))
         if not h:
             _check(-1)
         self._h = ctypes.c_void_p(h)

@@ -117,5 +117,8 @@ def test_argument_checks_before_any_cuda_call(gbaes):
     assert lib.aes_ctr_xcrypt(k.handle, None, 0, 0, big, big, 4, None) == -1  # NULL iv
     assert lib.aes_cbc_decrypt(k.handle, None, big, big, 4, None) == -1
     assert lib.aes_ctx_bits(k.handle) == 128 and lib.aes_ctx_bits(None) == -1
+    assert not lib.aes_pipeline_create_ex(0, 0, 2)  # unknown pipeline mode
+    assert b"mode" in lib.aes_last_error()
+    assert not lib.aes_pipeline_create_ex(24, 2, gbaes.PIPE_DIRECT)  # chunk not a multiple of 16
     msg = lib.aes_last_error()
     assert isinstance(msg, bytes) and len(msg) > 0

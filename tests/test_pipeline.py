@@ -1,4 +1,5 @@
-"""Host-buffer pipeline (chunks through device staging slots) against the oracle."""
+"""Host-buffer pipeline against the oracle: staged (chunks through device
+staging slots and copy engines) and direct (the kernel on the host buffers)."""
 import numpy as np
 import pytest
 
@@ -30,6 +31,25 @@ def test_pipeline_vs_oracle(gbaes, chunk, depth):
             assert np.array_equal(hout.numpy(), oracle.ecb(key, bits, data, decrypt=decrypt))
 
 
+@pytest.mark.parametrize("n", [1, 7, 2048 * 152 + 5, (5 << 20) // 16 + 7])
+def test_direct_pipeline_vs_oracle(gbaes, n):
+    """Direct mode at sizes below one tile, with a ragged last tile, and over several grid passes."""
+    rng = np.random.default_rng(n)
+    for bits in (128, 192, 256):
+        key = rng.integers(0, 256, bits // 8, dtype=np.uint8).tobytes()
+        k = gbaes.Key(key)
+        data = rng.integers(0, 256, 16 * n, dtype=np.uint8)
+        pipe = gbaes.Pipeline(mode=gbaes.PIPE_DIRECT)
+        for decrypt in (False, True):
+            hout = pipe.ecb(k, pinned(data), decrypt=decrypt)
+            torch.cuda.synchronize()
+            assert np.array_equal(hout.numpy(), oracle.ecb(key, bits, data, decrypt=decrypt))
+        h = pinned(data)  # in place
+        pipe.ecb(k, h, h)
+        torch.cuda.synchronize()
+        assert np.array_equal(h.numpy(), oracle.ecb(key, bits, data))
+
+
 def test_pipeline_in_place_and_errors(gbaes):
     rng = np.random.default_rng(3)
     key = rng.integers(0, 256, 16, dtype=np.uint8).tobytes()
@@ -48,6 +68,9 @@ def test_pipeline_in_place_and_errors(gbaes):
         pipe.ecb(k, pageable, h)
     with pytest.raises(gbaes.AesError):
         gbaes.Pipeline(24, 2)  # chunk not a multiple of 16
+    direct = gbaes.Pipeline(mode=gbaes.PIPE_DIRECT)
+    with pytest.raises(gbaes.AesError):
+        direct.ecb(k, pageable, h)
 
 
 def test_zero_copy_on_pinned_memory(gbaes):

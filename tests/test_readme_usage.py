@@ -45,10 +45,12 @@ def test_readme_usage(gbaes):
 
     host_in = torch.from_numpy(xs.copy()).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    gbaes.Pipeline().ecb(keys[0], host_in, host_out)
-    torch.cuda.synchronize()
     want = oracle.ecb(raw_keys[0], 128, xs)
-    assert np.array_equal(host_out.numpy(), want)
+    for mode in (gbaes.PIPE_DIRECT, gbaes.PIPE_STAGED):
+        host_out.zero_()
+        gbaes.Pipeline(mode=mode).ecb(keys[0], host_in, host_out)
+        torch.cuda.synchronize()
+        assert np.array_equal(host_out.numpy(), want)
     host_out.zero_()
     gbaes.ecb_ex(keys[0], host_in, host_out)
     torch.cuda.synchronize()
