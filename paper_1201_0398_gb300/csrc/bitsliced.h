@@ -18,7 +18,8 @@
 //    circuit without the constant, A the affine matrix), the inverse S-box of
 //    y is inv(A^-1 (y ^ 0x63)) = A^-1 F(A^-1 (y ^ 0x63)), the XOR with 0x63
 //    again folded into the round keys; A^-1 costs one three-input XOR per bit.
-//  * ShiftRows is a renaming of planes; MixColumns and AddRoundKey are XORs;
+//  * ShiftRows is a renaming of planes (across the two halves of a split state,
+//    see "half states" below); MixColumns and AddRoundKey are XORs;
 //    InvMixColumns is MixColumns after the preprocessing
 //    a0 ^= 4(a0^a2), a2 ^= 4(a0^a2), a1 ^= 4(a1^a3), a3 ^= 4(a1^a3).
 //
@@ -153,6 +154,17 @@ GBAES_HD constexpr void sbox_planes(uint32_t* x) {
     for (int i = 0; i < 8; ++i) x[7 - i] = o[i];
 }
 
+// S-box without its affine constant, then XOR with 8 key planes (k[t] for bit t),
+// in place: the key rides on the circuit's last XORs.
+GBAES_HD inline void sbox_planes_key(uint32_t* x, const uint32_t (&k)[8]) {
+    uint32_t u[8] = {}, o[8] = {};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) u[i] = x[7 - i];
+    sbox_circuit(u, o);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[7 - i] = o[i] ^ k[7 - i];
+}
+
 // Inverse S-box for input already XORed with the affine constant, in place:
 // A^-1 F(A^-1 x), F the circuit.
 GBAES_HD constexpr void inv_sbox_planes(uint32_t* x) {
@@ -209,96 +221,170 @@ GBAES_HD inline void xtime_planes(const uint32_t* a, uint32_t* y) {
     y[7] = a[6];
 }
 
+// Byte permute: byte i of the result is byte (sel >> 4i) & 7 of the eight
+// bytes {a (bytes 0-3), b (bytes 4-7)}; PRMT on the device.
+GBAES_HD inline uint32_t byte_perm(uint32_t a, uint32_t b, uint32_t sel) {
+#ifdef __CUDA_ARCH__
+    return __byte_perm(a, b, sel);
+#else
+    const uint64_t x = ((uint64_t)b << 32) | a;
+    uint32_t r = 0;
+    for (int i = 0; i < 4; ++i) r |= (uint32_t)((x >> (8 * ((sel >> (4 * i)) & 7u))) & 0xffu) << (8 * i);
+    return r;
+#endif
+}
+
 // 32x32 bit transpose in place: afterwards bit r of w[c] = old bit c of w[r].
+// Five exchange stages between words k and k+j (j = 16, 8, 4, 2, 1): word k
+// keeps its bits under the mask and takes the partner's, shifted up by j, in
+// the others; word k+j takes word k's, shifted down by j, under the mask.  The
+// j = 16 and j = 8 stages move whole bytes, one byte permute per word.
 GBAES_HD inline void transpose32(uint32_t* w) {
-    uint32_t m = 0x0000ffffu;
 #pragma unroll
-    for (int j = 16; j != 0; j >>= 1, m ^= (m << j)) {
+    for (int k = 0; k < 16; ++k) {
+        const uint32_t a = w[k], b = w[k + 16];
+        w[k] = byte_perm(a, b, 0x5410u);       // a.lo16 | b.lo16 << 16
+        w[k + 16] = byte_perm(a, b, 0x7632u);  // a.hi16 | b.hi16 << 16
+    }
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
+    for (int k = 0; k < 32; ++k)
+        if ((k & 8) == 0) {
+            const uint32_t a = w[k], b = w[k + 8];
+            w[k] = byte_perm(a, b, 0x6240u);      // bytes a0 b0 a2 b2
+            w[k + 8] = byte_perm(a, b, 0x7351u);  // bytes a1 b1 a3 b3
+        }
+    constexpr uint32_t kMask[3] = {0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int st = 0; st < 3; ++st) {
+        const int j = 4 >> st;
+        const uint32_t m = kMask[st], mh = m << j;
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
             if ((k & j) == 0) {
-                const uint32_t t = ((w[k] >> j) ^ w[k + j]) & m;
-                w[k] ^= t << j;
-                w[k + j] ^= t;
+                const uint32_t a = w[k], b = w[k + j];
+                w[k] = (a & ~mh) | ((b << j) & mh);
+                w[k + j] = ((a >> j) & m) | (b & ~m);
             }
-        }
     }
 }
 
-// Planes of state byte b live at s[8b .. 8b+7].  key(p) returns the key plane
-// (0 or all ones) of plane p for the round being applied.
+// ------------------------------------------------------------- half states
+//
+// The kernel splits one 32-block state between a pair of lanes: half h (0 or 1)
+// holds the 64 planes of state columns 2h and 2h+1.  Local byte l = 0..7 is
+// state byte 8h + l (row l % 4 of column 2h + l / 4), its planes at
+// s[8l .. 8l+7].  SubBytes, MixColumns and AddRoundKey stay inside a half;
+// ShiftRows sends four of the eight bytes to the other half.  `other(v, p)`
+// returns the other half's value of local plane p, v being this half's (on the
+// device: a lane shuffle of v; in the CPU test harness: a read of the other
+// thread's copy).
 
-// ShiftRows + MixColumns + AddRoundKey after SubBytes.  Output column c row r
-// takes input byte 4((c+r)%4)+r (ShiftRows: row r rotated left by r).
-template <class Key>
-GBAES_HD inline void shift_mix_add(uint32_t (&s)[128], const Key& key) {
-    uint32_t n[128];
+// ShiftRows, out(r, c) = in(r, c + r mod 4), on a half.  Row 0 (local bytes 0, 4)
+// stays; in row 1 local byte 1 takes local byte 5 and byte 5 the other half's
+// byte 1; row 2 (bytes 2, 6) comes from the other half's bytes 2, 6; in row 3
+// byte 3 takes the other half's byte 7 and byte 7 takes local byte 3.  (The same
+// rule holds for both halves, so one shuffle serves both.)
+template <class Other>
+GBAES_HD inline void shift_rows_half(uint32_t (&s)[64], const Other& other) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const uint32_t* a[4];
+    for (int t = 0; t < 8; ++t) {
+        const uint32_t b1 = s[8 + t], b2 = s[16 + t], b3 = s[24 + t];
+        const uint32_t b5 = s[40 + t], b6 = s[48 + t], b7 = s[56 + t];
+        s[8 + t] = b5;
+        s[40 + t] = other(b1, 8 + t);
+        s[16 + t] = other(b2, 16 + t);
+        s[48 + t] = other(b6, 48 + t);
+        s[24 + t] = other(b7, 56 + t);
+        s[56 + t] = b3;
+    }
+}
+
+// InvShiftRows, out(r, c) = in(r, c - r mod 4), on a half: byte 1 takes the other
+// half's byte 5, byte 5 takes local byte 1; bytes 2, 6 come from the other
+// half's 2, 6; byte 3 takes local byte 7, byte 7 the other half's byte 3.
+template <class Other>
+GBAES_HD inline void inv_shift_rows_half(uint32_t (&s)[64], const Other& other) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = &s[8 * (4 * ((c + r) & 3) + r)];
-        // 2a_r + 3a_{r+1} + a_{r+2} + a_{r+3} = xtime(t_r) + t_{r+1} + a_{r+3},  t_r = a_r + a_{r+1}
-        uint32_t tt[4][8];
+    for (int t = 0; t < 8; ++t) {
+        const uint32_t b1 = s[8 + t], b2 = s[16 + t], b3 = s[24 + t];
+        const uint32_t b5 = s[40 + t], b6 = s[48 + t], b7 = s[56 + t];
+        s[8 + t] = other(b5, 40 + t);
+        s[40 + t] = b1;
+        s[16 + t] = other(b2, 16 + t);
+        s[48 + t] = other(b6, 48 + t);
+        s[24 + t] = b7;
+        s[56 + t] = other(b3, 24 + t);
+    }
+}
+
+// Key planes of one half: step r, local byte l at base[kKeyStepWords*r + 8l .. +7].
+constexpr int kKeyHalfWords = 68;                 // 64 planes + 16 bytes, so the halves' rows use different banks
+constexpr int kKeyStepWords = 2 * kKeyHalfWords;  // both halves of one step
+
+struct HalfKeys {
+    const uint32_t* base;  // this half's planes of step 0 (16-byte aligned)
+    GBAES_HD void load8(int r, int l, uint32_t (&k)[8]) const {
+        const uint32_t* q = base + kKeyStepWords * r + 8 * l;
+#ifdef __CUDA_ARCH__
+        const uint4 x = reinterpret_cast<const uint4*>(q)[0], y = reinterpret_cast<const uint4*>(q)[1];
+        k[0] = x.x; k[1] = x.y; k[2] = x.z; k[3] = x.w;
+        k[4] = y.x; k[5] = y.y; k[6] = y.z; k[7] = y.w;
+#else
+        for (int t = 0; t < 8; ++t) k[t] = q[t];
+#endif
+    }
+};
+
+template <class Keys>
+GBAES_HD inline void add_key_half(uint32_t (&s)[64], const Keys& keys, int r) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+    for (int l = 0; l < 8; ++l) {
+        uint32_t k[8];
+        keys.load8(r, l, k);
 #pragma unroll
-            for (int t = 0; t < 8; ++t) tt[r][t] = a[r][t] ^ a[(r + 1) & 3][t];
+        for (int t = 0; t < 8; ++t) s[8 * l + t] ^= k[t];
+    }
+}
+
+// MixColumns on the half's two columns (after ShiftRows and SubBytes):
+// out_q = 2a_q + 3a_{q+1} + a_{q+2} + a_{q+3} = xtime(t_q) + t_{q+1} + a_{q+3},
+// t_q = a_q + a_{q+1}.  The round key was added before it, transformed (see
+// make_key_planes).
+GBAES_HD inline void mix_half(uint32_t (&s)[64]) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+    for (int c = 0; c < 2; ++c) {
+        uint32_t* a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = &s[8 * (4 * c + q)];
+        uint32_t tt[4][8], n[4][8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) tt[q][t] = a[q][t] ^ a[(q + 1) & 3][t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
             uint32_t x2[8];
-            xtime_planes(tt[r], x2);
+            xtime_planes(tt[q], x2);
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int p = 8 * (4 * c + r) + t;
-                n[p] = x2[t] ^ tt[(r + 1) & 3][t] ^ a[(r + 3) & 3][t] ^ key(p);
-            }
+            for (int t = 0; t < 8; ++t) n[q][t] = x2[t] ^ tt[(q + 1) & 3][t] ^ a[(q + 3) & 3][t];
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) a[q][t] = n[q][t];
     }
-#pragma unroll
-    for (int p = 0; p < 128; ++p) s[p] = n[p];
 }
 
-// ShiftRows + AddRoundKey (last encryption round).
-template <class Key>
-GBAES_HD inline void shift_add(uint32_t (&s)[128], const Key& key) {
-    uint32_t n[128];
+// AddRoundKey then InvMixColumns (MixColumns after the {04} preprocessing
+// a0 ^= 4(a0^a2), a2 ^= 4(a0^a2), a1 ^= 4(a1^a3), a3 ^= 4(a1^a3)) on the half's two columns.
+template <class Keys>
+GBAES_HD inline void add_inv_mix_half(uint32_t (&s)[64], const Keys& keys, int r) {
+    add_key_half(s, keys, r);
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < 2; ++c) {
+        uint32_t* a[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int p = 8 * (4 * c + r) + t;
-                n[p] = s[8 * (4 * ((c + r) & 3) + r) + t] ^ key(p);
-            }
-#pragma unroll
-    for (int p = 0; p < 128; ++p) s[p] = n[p];
-}
-
-// InvShiftRows: output column c row r takes input byte 4((c-r)%4)+r.
-GBAES_HD inline void inv_shift(uint32_t (&s)[128]) {
-    uint32_t n[128];
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int t = 0; t < 8; ++t) n[8 * (4 * c + r) + t] = s[8 * (4 * ((c + 4 - r) & 3) + r) + t];
-#pragma unroll
-    for (int p = 0; p < 128; ++p) s[p] = n[p];
-}
-
-// AddRoundKey then InvMixColumns (as MixColumns after the {04} preprocessing).
-template <class Key>
-GBAES_HD inline void add_inv_mix(uint32_t (&s)[128], const Key& key) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        uint32_t a[4][8];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int t = 0; t < 8; ++t) a[r][t] = s[8 * (4 * c + r) + t] ^ key(8 * (4 * c + r) + t);
+        for (int q = 0; q < 4; ++q) a[q] = &s[8 * (4 * c + q)];
         uint32_t e[8], e2[8], u4[8], o[8], o2[8], v4[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -316,87 +402,114 @@ GBAES_HD inline void add_inv_mix(uint32_t (&s)[128], const Key& key) {
             a[1][t] ^= v4[t];
             a[3][t] ^= v4[t];
         }
-        uint32_t tt[4][8];
+        uint32_t tt[4][8], n[4][8];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int t = 0; t < 8; ++t) tt[r][t] = a[r][t] ^ a[(r + 1) & 3][t];
+            for (int t = 0; t < 8; ++t) tt[q][t] = a[q][t] ^ a[(q + 1) & 3][t];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int q = 0; q < 4; ++q) {
             uint32_t x2[8];
-            xtime_planes(tt[r], x2);
+            xtime_planes(tt[q], x2);
 #pragma unroll
-            for (int t = 0; t < 8; ++t) s[8 * (4 * c + r) + t] = x2[t] ^ tt[(r + 1) & 3][t] ^ a[(r + 3) & 3][t];
+            for (int t = 0; t < 8; ++t) n[q][t] = x2[t] ^ tt[(q + 1) & 3][t] ^ a[(q + 3) & 3][t];
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) a[q][t] = n[q][t];
     }
 }
 
-template <class Key>
-GBAES_HD inline void add_key(uint32_t (&s)[128], const Key& key) {
+// SubBytes with the key planes of step r added to its output, on a half.
+template <class Keys>
+GBAES_HD inline void sub_bytes_key_half(uint32_t (&s)[64], const Keys& keys, int r) {
 #pragma unroll
-    for (int p = 0; p < 128; ++p) s[p] ^= key(p);
+    for (int l = 0; l < 8; ++l) {
+        uint32_t k[8];
+        keys.load8(r, l, k);
+        sbox_planes_key(&s[8 * l], k);
+    }
 }
 
-// Encryption of the 32 blocks held as planes; keys(r) gives round r's key
-// planes with the affine constant folded into rounds 1..nr.
-template <int NR, class Keys>
-GBAES_HD inline void encrypt_planes(uint32_t (&s)[128], const Keys& keys) {
-    add_key(s, keys.round(0));
+// Encryption of a half state, with the key planes of make_key_planes: step 0
+// before the first round, step r (the affine constant plus InvMixColumns of
+// round key r, so that MixColumns turns it into round key r) on the S-box
+// output of round r.  ShiftRows runs before SubBytes: the two commute, one
+// moving whole bytes and the other mapping each byte.
+template <int NR, class Keys, class Other>
+GBAES_HD inline void encrypt_half(uint32_t (&s)[64], const Keys& keys, const Other& other) {
+    add_key_half(s, keys, 0);
 #pragma unroll 1
     for (int r = 1; r < NR; ++r) {
-#pragma unroll
-        for (int b = 0; b < 16; ++b) sbox_planes(&s[8 * b]);
-        shift_mix_add(s, keys.round(r));
+        shift_rows_half(s, other);
+        sub_bytes_key_half(s, keys, r);
+        mix_half(s);
     }
-#pragma unroll
-    for (int b = 0; b < 16; ++b) sbox_planes(&s[8 * b]);
-    shift_add(s, keys.round(NR));
+    shift_rows_half(s, other);
+    sub_bytes_key_half(s, keys, NR);
 }
 
-// Straight inverse cipher; keys(r) gives the key planes applied at step r
-// (r = 0: the last encryption round key, ...), constant folded as described.
-template <int NR, class Keys>
-GBAES_HD inline void decrypt_planes(uint32_t (&s)[128], const Keys& keys) {
-    add_key(s, keys.round(0));
+// Straight inverse cipher on a half state; keys step r as make_key_planes gives it.
+template <int NR, class Keys, class Other>
+GBAES_HD inline void decrypt_half(uint32_t (&s)[64], const Keys& keys, const Other& other) {
+    add_key_half(s, keys, 0);
 #pragma unroll 1
     for (int r = 1; r < NR; ++r) {
-        inv_shift(s);
+        inv_shift_rows_half(s, other);
 #pragma unroll
-        for (int b = 0; b < 16; ++b) inv_sbox_planes(&s[8 * b]);
-        add_inv_mix(s, keys.round(r));
+        for (int l = 0; l < 8; ++l) inv_sbox_planes(&s[8 * l]);
+        add_inv_mix_half(s, keys, r);
     }
-    inv_shift(s);
+    inv_shift_rows_half(s, other);
 #pragma unroll
-    for (int b = 0; b < 16; ++b) inv_sbox_planes(&s[8 * b]);
-    add_key(s, keys.round(NR));
+    for (int l = 0; l < 8; ++l) inv_sbox_planes(&s[8 * l]);
+    add_key_half(s, keys, NR);
+}
+
+// InvMixColumns of one column word (byte q = row q): out_q = {0e}b_q + {0b}b_{q+1}
+// + {0d}b_{q+2} + {09}b_{q+3}.
+GBAES_HD constexpr uint8_t xtime8(uint8_t b) { return (uint8_t)((b << 1) ^ ((b & 0x80u) ? 0x1bu : 0u)); }
+GBAES_HD constexpr uint32_t inv_mix_word(uint32_t w) {
+    uint8_t b[4] = {}, o[4] = {};
+    for (int q = 0; q < 4; ++q) b[q] = (uint8_t)(w >> (8 * q));
+    for (int q = 0; q < 4; ++q) {
+        const uint8_t x = b[q], y = b[(q + 1) & 3], z = b[(q + 2) & 3], v = b[(q + 3) & 3];
+        const uint8_t x2 = xtime8(x), x4 = xtime8(x2), x8 = xtime8(x4);  // {0e} = 8 + 4 + 2
+        const uint8_t y2 = xtime8(y), y8 = xtime8(xtime8(y2));          // {0b} = 8 + 2 + 1
+        const uint8_t z4 = xtime8(xtime8(z)), z8 = xtime8(z4);          // {0d} = 8 + 4 + 1
+        const uint8_t v8 = xtime8(xtime8(xtime8(v)));                   // {09} = 8 + 1
+        o[q] = (uint8_t)(x8 ^ x4 ^ x2 ^ y8 ^ y2 ^ y ^ z8 ^ z4 ^ z ^ v8 ^ v);
+    }
+    return (uint32_t)o[0] | (uint32_t)o[1] << 8 | (uint32_t)o[2] << 16 | (uint32_t)o[3] << 24;
 }
 
 // Key planes (0 or all ones) for each processing step, from a round-key
-// schedule rk (4*(nr+1) words).  Encryption: step r uses rk[r], XORed with
-// 0x63 in every byte for r >= 1.  Decryption (straight inverse cipher): step r
-// uses rk[nr - r], XORed with 0x63 in every byte for r < nr.
+// schedule rk (4*(nr+1) words), plane p = 8*(state byte) + bit.
+// Encryption: step 0 is rk[0]; step r (1 <= r < nr) is InvMixColumns(rk[r])
+// XOR 0x63 in every byte, added to the S-box output before MixColumns
+// (MixColumns is linear and maps 0x63 in all four bytes of a column to
+// itself); step nr is rk[nr] XOR 0x63.  Decryption (straight inverse cipher):
+// step r uses rk[nr - r], XORed with 0x63 in every byte for r < nr.
 GBAES_HD inline void make_key_planes(const uint32_t* rk, int nr, bool decrypt, uint32_t (*planes)[128]) {
     for (int r = 0; r <= nr; ++r) {
         const int src = decrypt ? nr - r : r;
         const bool fold = decrypt ? (r < nr) : (r >= 1);
         for (int p = 0; p < 128; ++p) {
-            const uint32_t w = rk[4 * src + p / 32] ^ (fold ? 0x63636363u : 0u);
+            uint32_t w = rk[4 * src + p / 32];
+            if (!decrypt && r >= 1 && r < nr) w = inv_mix_word(w);
+            if (fold) w ^= 0x63636363u;
             planes[r][p] = ((w >> (p % 32)) & 1u) ? 0xffffffffu : 0u;
         }
     }
 }
 
-// Round-key planes of one step, read by plane index.
-struct StepKey {
-    const uint32_t* k;
-    GBAES_HD uint32_t operator()(int p) const { return k[p]; }
-};
-
-// All steps' key planes (e.g. in the kernel parameters).
-struct PlaneKeys {
-    const uint32_t (*planes)[128];
-    GBAES_HD StepKey round(int r) const { return StepKey{planes[r]}; }
-};
+// Lays make_key_planes' output out for HalfKeys: step r, half h, local plane q
+// at out[kKeyStepWords*r + kKeyHalfWords*h + q] (q = p - 64h).
+GBAES_HD inline void split_key_planes(const uint32_t (*planes)[128], int nr, uint32_t* out) {
+    for (int r = 0; r <= nr; ++r)
+        for (int p = 0; p < 128; ++p) out[kKeyStepWords * r + kKeyHalfWords * (p / 64) + p % 64] = planes[r][p];
+}
 
 }  // namespace bs
 }  // namespace gbaes

@@ -1,13 +1,19 @@
 // Bitsliced AES-ECB kernel (the Boolean-circuit alternative to Eq. 1's tables).
 //
-// Each thread holds 32 blocks as 128 bit planes (bitsliced.h): a warp loads
-// 1,024 consecutive blocks with coalesced 16-byte loads (lane l takes blocks
-// base + 32k + l, k = 0..31), each thread transposes its four 32x32 bit
-// matrices in registers, runs the rounds as bitwise logic with no memory
-// lookups at all, transposes back and stores.  Round-key planes (0 or all
-// ones, the S-box's affine constant folded in) travel in the kernel's large
-// parameter block.  The kernel is bound by the integer pipe, not by shared
-// memory: it is the measured counterpart to the T-table kernel.
+// A pair of lanes holds 32 blocks as 128 bit planes (bitsliced.h), split by
+// state columns: lane 2g+h holds the 64 planes of columns 2h and 2h+1 of the 32
+// blocks of its pair g.  A warp takes 512 consecutive blocks: pair g owns
+// blocks base + 16k + g (k = 0..31) and lane h loads bytes 8h..8h+15 of each
+// with a coalesced 8-byte load (the warp reads 256 contiguous bytes per load),
+// transposes its two 32x32 bit matrices in registers, runs the rounds as
+// bitwise logic with no memory lookups (ShiftRows trades four bytes' planes
+// with the other lane of the pair by shuffle), transposes back and stores.
+// Splitting the state halves the registers a lane needs (four CTAs of 128
+// threads per SM instead of two) and the unrolled round body each lane runs.
+// Round-key planes (0 or all ones, the S-box's affine constant folded in) are
+// staged once per CTA in shared memory, each half's row in its own banks.  The
+// kernel is bound by the integer pipe, not by shared memory: it is the measured
+// counterpart to the T-table kernel.
 #include <mutex>
 
 #include "bitsliced.h"
@@ -15,43 +21,54 @@
 
 namespace gbaes {
 
+constexpr int kBsThreads = 128;
+constexpr int kBsCtasPerSm = 4;
+constexpr int kBsWarpBlocks = 512;  // 16 lane pairs x 32 blocks
+
 struct BsArgs {
     const uint4* in;
     uint4* out;
     uint64_t nblocks;
-    uint32_t planes[15][128];  // key planes per step (7,680 bytes)
+    uint32_t planes[15 * bs::kKeyStepWords];  // split_key_planes layout (8,160 bytes)
+};
+
+// The other lane of the pair (lane ^ 1) hands over its copy of the plane.
+struct PairShuffle {
+    __device__ uint32_t operator()(uint32_t v, int) const { return __shfl_xor_sync(0xffffffffu, v, 1); }
 };
 
 template <int NR, bool DEC>
-__global__ void __launch_bounds__(128) bitsliced_kernel(const __grid_constant__ BsArgs a) {
+__global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitsliced_kernel(const __grid_constant__ BsArgs a) {
+    __shared__ __align__(16) uint32_t keys_s[(NR + 1) * bs::kKeyStepWords];
+    for (int i = threadIdx.x; i < (NR + 1) * bs::kKeyStepWords; i += blockDim.x) keys_s[i] = a.planes[i];
+    __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t h = lane & 1u, g = lane >> 1;
+    const bs::HalfKeys keys{keys_s + bs::kKeyHalfWords * h};
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const bs::PlaneKeys keys{a.planes};
-    for (uint64_t base = warp * 1024; base < a.nblocks; base += nwarps * 1024) {
-        uint32_t s[128];
+    for (uint64_t base = warp * kBsWarpBlocks; base < a.nblocks; base += nwarps * kBsWarpBlocks) {
+        uint32_t s[64];
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
-            const uint64_t idx = base + 32u * k + lane;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (idx < a.nblocks) v = __ldcs(a.in + idx);
+            const uint64_t idx = base + 16u * k + g;
+            uint2 v = make_uint2(0, 0);
+            if (idx < a.nblocks) v = __ldcs(reinterpret_cast<const uint2*>(a.in + idx) + h);
             s[k] = v.x;
             s[32 + k] = v.y;
-            s[64 + k] = v.z;
-            s[96 + k] = v.w;
         }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) bs::transpose32(&s[32 * i]);  // s[32i + j] = plane 32i + j
+        bs::transpose32(&s[0]);  // s[32i + j] = bit j of word 2h + i: local plane 32i + j
+        bs::transpose32(&s[32]);
         if (DEC)
-            bs::decrypt_planes<NR>(s, keys);
+            bs::decrypt_half<NR>(s, keys, PairShuffle{});
         else
-            bs::encrypt_planes<NR>(s, keys);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) bs::transpose32(&s[32 * i]);
+            bs::encrypt_half<NR>(s, keys, PairShuffle{});
+        bs::transpose32(&s[0]);
+        bs::transpose32(&s[32]);
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
-            const uint64_t idx = base + 32u * k + lane;
-            if (idx < a.nblocks) __stcs(a.out + idx, make_uint4(s[k], s[32 + k], s[64 + k], s[96 + k]));
+            const uint64_t idx = base + 16u * k + g;
+            if (idx < a.nblocks) __stcs(reinterpret_cast<uint2*>(a.out + idx) + h, make_uint2(s[k], s[32 + k]));
         }
     }
 }
@@ -79,26 +96,28 @@ int launch_bitsliced(const EcbArgs& e, const uint32_t* enc_rk, int nr, Mode mode
     const bool dec = mode == kDec;
     BsKernel fn = pick_bs(nr, dec);
     if (!fn) return fail(AES_ERR_ARG, "no bitsliced kernel for nr=%d", nr);
-    if (threads % 32 || threads < 32 || threads > 128) threads = 128;
-    static BsArgs a;  // 7.7 KB: built here, copied into the launch by value
+    (void)threads;  // the kernel's shape is fixed by its register budget: 128 threads, 4 CTAs per SM
+    static BsArgs a;  // 8.2 KB: built here, copied into the launch by value
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);
     a.in = e.in;
     a.out = e.out;
     a.nblocks = e.nblocks;
-    bs::make_key_planes(enc_rk, nr, dec, a.planes);
+    uint32_t planes[15][128];
+    bs::make_key_planes(enc_rk, nr, dec, planes);
+    bs::split_key_planes(planes, nr, a.planes);
     DeviceInfo info;
     int rc = current_device_info(&info);
     if (rc) return rc;
     int per_sm = 0;
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBsThreads, 0);
     if (err != cudaSuccess || per_sm < 1) per_sm = 1;
-    const uint64_t tiles = (e.nblocks + 1023) / 1024;  // one warp tile = 1,024 blocks
-    const uint64_t warps_per_cta = (uint64_t)threads / 32;
+    const uint64_t tiles = (e.nblocks + kBsWarpBlocks - 1) / kBsWarpBlocks;
+    const uint64_t warps_per_cta = kBsThreads / 32;
     uint64_t grid = (uint64_t)info.sms * per_sm;
     const uint64_t need = (tiles + warps_per_cta - 1) / warps_per_cta;
     if (need < grid) grid = need;
-    fn<<<(unsigned)grid, threads, 0, stream>>>(a);
+    fn<<<(unsigned)grid, kBsThreads, 0, stream>>>(a);
     err = cudaGetLastError();
     if (err != cudaSuccess) return fail(AES_ERR_CUDA, "bitsliced kernel launch: %s", cudaGetErrorString(err));
     return AES_OK;

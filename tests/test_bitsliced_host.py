@@ -1,6 +1,9 @@
-"""The bitsliced circuit (csrc/bitsliced.h) compiled for the CPU by a test
-harness and compared with the oracle: transposes, the S-box circuit, the
-folded affine constant, MixColumns / InvMixColumns and the key planes."""
+"""The bitsliced cipher (csrc/bitsliced.h) compiled for the CPU by a test
+harness and compared with the oracle: the state split between two halves as in
+the kernel (each half on its own host thread, the lane shuffle replaced by a
+read of the other thread's plane), the byte-permute transposes, the S-box
+circuit, ShiftRows across the halves, MixColumns / InvMixColumns and the key
+planes with the affine constant and InvMixColumns folded in."""
 import os
 import subprocess
 import sys
@@ -17,7 +20,7 @@ CSRC = os.path.join(os.path.dirname(HERE), "paper_1201_0398_gb300", "csrc")
 @pytest.fixture(scope="module")
 def harness(tmp_path_factory):
     exe = str(tmp_path_factory.mktemp("bs") / "bitsliced_check")
-    subprocess.run(["g++", "-std=c++17", "-O1", "-Wno-unknown-pragmas", "-I", CSRC,
+    subprocess.run(["g++", "-std=c++17", "-O1", "-pthread", "-Wno-unknown-pragmas", "-I", CSRC,
                     os.path.join(HERE, "bitsliced_check.cpp"), "-o", exe], check=True)
     return exe
 

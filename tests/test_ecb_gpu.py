@@ -262,17 +262,18 @@ def test_sweep_top_sizes_sampled(gbaes, gib):
 
 @pytest.mark.parametrize("bits", BITS)
 def test_bitsliced_kernel_vs_oracle(gbaes, bits):
-    """The Boolean-circuit kernel (32 blocks per thread as bit planes): edge sizes
-    around a warp tile (1,024 blocks) and a multi-CTA run with a ragged tail."""
+    """The Boolean-circuit kernel (a lane pair holds 32 blocks as bit planes, split
+    by state columns; a warp takes 512 blocks, a CTA 2,048): edge sizes around a
+    pair's, a warp's and a CTA's tile, and more than one pass of the full grid
+    (152 SMs x 4 CTAs x 2,048 blocks) with a ragged tail."""
     rng = np.random.default_rng(900 + bits)
     key = rng.integers(0, 256, bits // 8, dtype=np.uint8).tobytes()
     k = gbaes.Key(key)
-    for n in (1, 31, 32, 33, 1023, 1024, 1025, 4097, sms() * 512 + 3):
+    for n in (1, 15, 16, 17, 31, 33, 511, 512, 513, 2047, 2049, 4097, sms() * 4 * 2048 + 2048 * 3 + 5):
         data = rng.integers(0, 256, 16 * n, dtype=np.uint8)
         for decrypt in (False, True):
-            for threads in (64, 128):
-                out = gbaes.ecb_ex(k, dev(data), decrypt=decrypt, kernel=gbaes.KERNEL_BITSLICED, threads=threads)
-                assert np.array_equal(host(out), oracle.ecb(key, bits, data, decrypt=decrypt)), (n, decrypt)
+            out = gbaes.ecb_ex(k, dev(data), decrypt=decrypt, kernel=gbaes.KERNEL_BITSLICED)
+            assert np.array_equal(host(out), oracle.ecb(key, bits, data, decrypt=decrypt)), (n, decrypt)
 
 
 def test_bitsliced_equals_table_kernel_large(gbaes):
