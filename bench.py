@@ -58,6 +58,11 @@ NR = {128: 10, 192: 12, 256: 14}
 GiB = 1 << 30
 MiB = 1 << 20
 LOOKUPS_PER_CLK_PER_SM = 32  # 32 banks x 4 B: one conflict-free 32-bit lookup per lane per clock
+ALU_LANES_PER_CLK_PER_SM = 64  # integer ALU pipe: 4 SM sub-partitions x 16 lanes
+# The bitsliced kernel's integer-ALU instructions per 16-byte block, (Nr, decrypt) -> lane-ops, counted by ncu
+# (ALU-pipe utilisation x 2 warp instructions per clock per SM x active cycles x SMs x 32 / blocks) in
+# profiles/bitsliced_kernel_ecb_64MiB_ncu_full.md.
+BITSLICED_ALU_OPS_PER_BLOCK = {(10, 0): 683.2, (10, 1): 826.9}
 
 
 def parse_args():
@@ -442,13 +447,24 @@ def run_ours(args):
         clock_frac = dom["gbs"] / r_clk
     roofline = {
         "bound": "smem", "achieved": dom["gbs"], "peak": dom["smem_roofline_gbs"], "unit": "GB/s",
-        "frac": dom["frac"], "traffic": traffic, "kernel": ktpl if kernel == g.KERNEL_TABLE else "bitsliced",
+        "frac": dom["frac"], "traffic": traffic, "kernel": ktpl,
         "peak_basis": (f"{sms} SMs x {LOOKUPS_PER_CLK_PER_SM} lookups/clk x {f_max / 1e6:.0f} MHz "
                        f"({peak_kind} sm_max_mhz) / {NR[bits_dom]} lookups per plaintext byte"),
         "frac_at_measured_clock": clock_frac,
         "hbm": {"achieved": 2 * dom["gbs"], "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                 "frac": dom["hbm_frac"], "peak_kind": f"{peak_kind} hbm_gbs (copy)"},
     }
+    if kernel == g.KERNEL_BITSLICED:  # bound by the integer ALU pipe, not by shared memory
+        ops_blk = BITSLICED_ALU_OPS_PER_BLOCK.get((NR[bits_dom], int(dec_dom)))
+        peak = sms * ALU_LANES_PER_CLK_PER_SM * f_max / ops_blk * 16 / 1e9 if ops_blk else None
+        roofline.update({
+            "bound": "alu", "peak": peak, "frac": dom["gbs"] / peak if peak else None,
+            "kernel": f"bitsliced_kernel<{NR[bits_dom]},{int(dec_dom)}>",
+            "peak_basis": (f"{sms} SMs x {ALU_LANES_PER_CLK_PER_SM} ALU lanes/clk x {f_max / 1e6:.0f} MHz / "
+                           f"{ops_blk} ALU ops per 16-byte block (ncu)" if ops_blk else
+                           "no ncu count of ALU ops per block for this launch"),
+            "frac_at_measured_clock": (dom["gbs"] / (peak * clk["sm_mhz"] * 1e6 / f_max)
+                                       if peak and clk.get("sm_mhz") else None)})
 
     # ---- e2e: pinned host buffers, copies inside the timed region
     e2e = None
@@ -810,9 +826,10 @@ def run_profile_case(args):
       table      256 MiB, AES-128 encryption + AES-256 decryption, table kernel
       table1g    1 GiB, the bench's launches (AES-128/192/256, encrypt + decrypt),
                  for single-pass DRAM-byte captures at the bench size only
-      bitsliced  64 MiB, AES-128 encryption + decryption, bitsliced kernel
+      bitsliced  64 MiB, AES-128 encryption + decryption, then AES-256 encryption +
+                 decryption, bitsliced kernel
       batch      10,000 messages, 16 B - 1 MiB (~0.95 GB), one batched launch each
-      sweep      one AES-128 encryption per size, 4 KiB - 1 GiB: table (size-dispatched),
+      sweep      one AES-128 encryption per size, 4 KiB - 256 MiB: table (size-dispatched),
                  compact tables (up to 64 MiB), replicated tables, bitsliced
       singles    the 10,000-message batch as one batched launch, then as 10,000
                  single-message launches
@@ -828,7 +845,8 @@ def run_profile_case(args):
     if case in ("table", "table1g", "bitsliced"):
         kid = g.KERNEL_BITSLICED if case == "bitsliced" else g.KERNEL_TABLE
         size = {"table": 256 << 20, "table1g": GiB, "bitsliced": 64 << 20}[case]
-        ops = {"table": [(128, False), (256, True)], "bitsliced": [(128, False), (128, True)],
+        ops = {"table": [(128, False), (256, True)],
+               "bitsliced": [(128, False), (128, True), (256, False), (256, True)],
                "table1g": [(b, d) for b in BITS for d in (False, True)]}[case]
         x = workloads.device_bytes(1, size)
         y = torch.empty_like(x)
@@ -837,11 +855,11 @@ def run_profile_case(args):
             for bits, dec in ops:
                 g.ecb_ex(keys[bits], x, y, decrypt=dec, kernel=kid)
     elif case == "sweep":
-        x = workloads.device_bytes(31, GiB)
+        x = workloads.device_bytes(31, 256 * MiB)
         y = torch.empty_like(x)
         k = g.Key(workloads.random_key(168, 128))
         for kid in (g.KERNEL_TABLE, g.KERNEL_TABLE_COMPACT, g.KERNEL_TABLE_REPLICATED, g.KERNEL_BITSLICED):
-            for size in (4096 * 4 ** i for i in range(10)):  # 4 KiB .. 1 GiB
+            for size in (4096 * 4 ** i for i in range(9)):  # 4 KiB .. 256 MiB
                 if kid != g.KERNEL_TABLE_COMPACT or size <= 64 * MiB:
                     g.ecb_ex(k, x[:size], y[:size], kernel=kid)
     else:
