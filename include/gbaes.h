@@ -193,7 +193,7 @@ int aes_ecb_batch(const aes_msg_desc* msgs, size_t nmsg, const aes_ctx* const* c
  *    AES_ERR_ARG; the 10,000-message, 10,000-key batch needs about 5.6 MiB.
  *  - The first call in each CUDA context (normally once per device, in its
  *    primary context) looks up the array's device address there
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) and keeps it for that context.
  *  - Every call shares the one array and overwrites it (the tile counter is
  *    re-zeroed by each call's upload).  Calls whose work overlaps on the GPU
  *    -- on different streams, or from different host threads -- race on it;
