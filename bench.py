@@ -826,7 +826,7 @@ def run_profile_case(args):
       table      256 MiB, AES-128 encryption + AES-256 decryption, table kernel
       table1g    1 GiB, the bench's launches (AES-128/192/256, encrypt + decrypt),
                  for single-pass DRAM-byte captures at the bench size only
-      bitsliced  64 MiB, AES-128 encryption + decryption, then AES-256 encryption +
+      bitsliced  256 MiB, AES-128 encryption + decryption, then AES-256 encryption +
                  decryption, bitsliced kernel
       batch      10,000 messages, 16 B - 1 MiB (~0.95 GB), one batched launch each
       sweep      one AES-128 encryption per size, 4 KiB - 256 MiB: table (size-dispatched),
@@ -844,7 +844,7 @@ def run_profile_case(args):
     case, warm, launches = args.profile_case, args.profile_warmup, args.profile_launches
     if case in ("table", "table1g", "bitsliced"):
         kid = g.KERNEL_BITSLICED if case == "bitsliced" else g.KERNEL_TABLE
-        size = {"table": 256 << 20, "table1g": GiB, "bitsliced": 64 << 20}[case]
+        size = {"table": 256 << 20, "table1g": GiB, "bitsliced": 256 << 20}[case]
         ops = {"table": [(128, False), (256, True)],
                "bitsliced": [(128, False), (128, True), (256, False), (256, True)],
                "table1g": [(b, d) for b in BITS for d in (False, True)]}[case]
