@@ -29,7 +29,8 @@ def _sources():
 
 def _fingerprint() -> str:
     h = hashlib.sha256()
-    files = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + sorted(glob.glob(os.path.join(INCLUDE, "*.h")))
+    files = (_sources() + sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")))
+             + sorted(glob.glob(os.path.join(INCLUDE, "*.h"))))
     for f in files + [os.path.abspath(__file__)]:
         h.update(f.encode())
         with open(f, "rb") as fh:

@@ -31,6 +31,7 @@
 #include <cstdint>
 
 #include "aes_tables.h"
+#include "sbox_lut3.h"
 
 #ifndef __CUDACC__
 #define GBAES_HD
@@ -154,15 +155,42 @@ GBAES_HD constexpr void sbox_planes(uint32_t* x) {
     for (int i = 0; i < 8; ++i) x[7 - i] = o[i];
 }
 
+// Three-input lookup table: bit i of imm is the result for operand bits (a, b, c) =
+// (i >> 2 & 1, i >> 1 & 1, i & 1), applied to 32 bit positions at once.  Lop3Eval
+// evaluates it with plain logic (usable in constant expressions); Lop3 issues
+// PTX lop3 on the device, one LOP3 instruction.
+struct Lop3Eval {
+    GBAES_HD constexpr uint32_t operator()(uint32_t a, uint32_t b, uint32_t c, uint32_t imm) const {
+        uint32_t r = 0;
+        for (uint32_t i = 0; i < 8; ++i)
+            if ((imm >> i) & 1u) r |= ((i & 4u) ? a : ~a) & ((i & 2u) ? b : ~b) & ((i & 1u) ? c : ~c);
+        return r;
+    }
+};
+struct Lop3 {
+#ifdef __CUDA_ARCH__
+    template <class Imm>
+    __device__ __forceinline__ uint32_t operator()(uint32_t a, uint32_t b, uint32_t c, Imm) const {
+        uint32_t d;
+        asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(Imm::value));
+        return d;
+    }
+#else
+    constexpr uint32_t operator()(uint32_t a, uint32_t b, uint32_t c, uint32_t imm) const {
+        return Lop3Eval{}(a, b, c, imm);
+    }
+#endif
+};
+
 // S-box without its affine constant, then XOR with 8 key planes (k[t] for bit t),
-// in place: the key rides on the circuit's last XORs.
-GBAES_HD inline void sbox_planes_key(uint32_t* x, const uint32_t (&k)[8]) {
-    uint32_t u[8] = {}, o[8] = {};
-#pragma unroll
-    for (int i = 0; i < 8; ++i) u[i] = x[7 - i];
-    sbox_circuit(u, o);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) x[7 - i] = o[i] ^ k[7 - i];
+// in place on one byte's 8 planes: the circuit mapped onto three-input tables
+// (sbox_lut3.h), the key riding on its last tables.
+GBAES_HD inline void sbox_planes_key(uint32_t* x, const uint32_t (&k)[8]) { sbox_key_lut3(x, k, Lop3{}); }
+
+// Inverse S-box then XOR with 8 key planes, in place, for input already XORed
+// with the affine constant: A^-1 F(A^-1 x) ^ k as three-input tables.
+GBAES_HD inline void inv_sbox_planes_key(uint32_t* x, const uint32_t (&k)[8]) {
+    inv_sbox_key_lut3(x, k, Lop3{});
 }
 
 // Inverse S-box for input already XORed with the affine constant, in place:
@@ -208,6 +236,36 @@ constexpr bool check_sbox_circuit() {
     return true;
 }
 static_assert(check_sbox_circuit(), "the S-box circuit does not reproduce the S-box");
+
+// The same, exhaustively, for the table-mapped networks the kernel runs, with all-zero
+// and all-one key planes: S(x) ^ key and S^-1(x) ^ key.
+constexpr bool check_sbox_lut3() {
+    for (int key = 0; key < 256; key += 255)
+        for (int g = 0; g < 8; ++g) {
+            uint32_t fwd[8] = {}, inv[8] = {}, kp[8] = {};
+            for (int t = 0; t < 8; ++t) {
+                kp[t] = ((key >> t) & 1) ? 0xffffffffu : 0u;
+                for (int k = 0; k < 32; ++k) {
+                    const int x = 32 * g + k;
+                    fwd[t] |= (uint32_t)((x >> t) & 1) << k;
+                    inv[t] |= (uint32_t)(((x ^ 0x63) >> t) & 1) << k;
+                }
+            }
+            sbox_key_lut3(fwd, kp, Lop3Eval{});
+            inv_sbox_key_lut3(inv, kp, Lop3Eval{});
+            for (int k = 0; k < 32; ++k) {
+                const int x = 32 * g + k;
+                int f = 0, i = 0;
+                for (int t = 0; t < 8; ++t) {
+                    f |= (int)((fwd[t] >> k) & 1) << t;
+                    i |= (int)((inv[t] >> k) & 1) << t;
+                }
+                if ((f ^ 0x63 ^ key) != kAesTables.sbox[x] || (i ^ key) != kAesTables.inv_sbox[x]) return false;
+            }
+        }
+    return true;
+}
+static_assert(check_sbox_lut3(), "the table-mapped S-box networks do not reproduce the S-box");
 
 // Multiplication by {02} on one byte's planes (t[0] = least significant bit).
 GBAES_HD inline void xtime_planes(const uint32_t* a, uint32_t* y) {
@@ -375,11 +433,9 @@ GBAES_HD inline void mix_half(uint32_t (&s)[64]) {
     }
 }
 
-// AddRoundKey then InvMixColumns (MixColumns after the {04} preprocessing
-// a0 ^= 4(a0^a2), a2 ^= 4(a0^a2), a1 ^= 4(a1^a3), a3 ^= 4(a1^a3)) on the half's two columns.
-template <class Keys>
-GBAES_HD inline void add_inv_mix_half(uint32_t (&s)[64], const Keys& keys, int r) {
-    add_key_half(s, keys, r);
+// InvMixColumns (MixColumns after the {04} preprocessing a0 ^= 4(a0^a2),
+// a2 ^= 4(a0^a2), a1 ^= 4(a1^a3), a3 ^= 4(a1^a3)) on the half's two columns.
+GBAES_HD inline void inv_mix_half(uint32_t (&s)[64]) {
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         uint32_t* a[4];
@@ -450,21 +506,31 @@ GBAES_HD inline void encrypt_half(uint32_t (&s)[64], const Keys& keys, const Oth
     sub_bytes_key_half(s, keys, NR);
 }
 
-// Straight inverse cipher on a half state; keys step r as make_key_planes gives it.
+// InvSubBytes with the key planes of step r added to its output, on a half.
+template <class Keys>
+GBAES_HD inline void inv_sub_bytes_key_half(uint32_t (&s)[64], const Keys& keys, int r) {
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+        uint32_t k[8];
+        keys.load8(r, l, k);
+        inv_sbox_planes_key(&s[8 * l], k);
+    }
+}
+
+// Straight inverse cipher on a half state; keys step r as make_key_planes gives
+// it, added on the inverse S-box output (before InvMixColumns, as the cipher
+// orders it).
 template <int NR, class Keys, class Other>
 GBAES_HD inline void decrypt_half(uint32_t (&s)[64], const Keys& keys, const Other& other) {
     add_key_half(s, keys, 0);
 #pragma unroll 1
     for (int r = 1; r < NR; ++r) {
         inv_shift_rows_half(s, other);
-#pragma unroll
-        for (int l = 0; l < 8; ++l) inv_sbox_planes(&s[8 * l]);
-        add_inv_mix_half(s, keys, r);
+        inv_sub_bytes_key_half(s, keys, r);
+        inv_mix_half(s);
     }
     inv_shift_rows_half(s, other);
-#pragma unroll
-    for (int l = 0; l < 8; ++l) inv_sbox_planes(&s[8 * l]);
-    add_key_half(s, keys, NR);
+    inv_sub_bytes_key_half(s, keys, NR);
 }
 
 // InvMixColumns of one column word (byte q = row q): out_q = {0e}b_q + {0b}b_{q+1}

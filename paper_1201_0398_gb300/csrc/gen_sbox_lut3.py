@@ -1,0 +1,278 @@
+"""Writes sbox_lut3.h: the bitsliced S-box circuits mapped onto three-input lookup tables.
+
+The bitsliced kernel spends most of its integer-ALU instructions in the S-box
+circuit (bitsliced.h, `sbox_circuit`: Boyar and Peralta's depth-16 circuit, 34
+ANDs and 94 XORs).  A GPU evaluates any Boolean function of three 32-bit
+operands in one LOP3 instruction, so the cheapest program for the circuit is a
+cover of its gates by three-input cones.  This script
+
+  1. reads the gate list of `sbox_circuit` from bitsliced.h (one source for the
+     circuit; its exhaustive compile-time check stays where it is),
+  2. builds the two networks the kernel evaluates per state byte: the S-box with
+     a round-key plane XORed onto each output bit (encryption), and the inverse
+     S-box A^-1 F(A^-1 x) with the same key XOR (decryption; A^-1 the inverse of
+     the S-box's affine matrix, F the circuit),
+  3. maps each network onto three-input lookup tables: every 3-feasible cut of
+     every gate is enumerated, each gate takes the cut of least area flow, and
+     passes of exact-area recovery then re-choose cuts where that frees the most
+     tables (the standard cut-based technology-mapping method of FPGA tools),
+  4. emits each table as one `lop(a, b, c, truth_table)` call, the truth table in
+     PTX's lop3 encoding (bit i = F(i >> 2 & 1, i >> 1 & 1, i & 1) for operands
+     a, b, c), in the order the network computes them.
+
+Run from anywhere: python gen_sbox_lut3.py  (rewrites sbox_lut3.h next to it).
+"""
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def circuit_gates():
+    """(out, op, a, b) for each gate of sbox_circuit, inputs u0..u7, outputs s0..s7."""
+    src = open(os.path.join(HERE, "bitsliced.h")).read()
+    body = src[src.index("GBAES_HD constexpr void sbox_circuit"):]
+    body = body[:body.index("\n}\n")]
+    gates, seen = [], set()
+    for m in re.finditer(r"(\w+(?:\[\d\])?)\s*=\s*(\w+(?:\[\d\])?)\s*([\^&])\s*(\w+(?:\[\d\])?)", body):
+        out, a, op, b = (re.sub(r"\[(\d)\]", r"\1", g) for g in m.groups())
+        if out not in seen:
+            seen.add(out)
+            gates.append((out, op, a, b))
+    assert len(gates) == 128 and sum(g[1] == "&" for g in gates) == 34
+    return gates
+
+
+def affine_inverse_rows():
+    """Rows of A^-1 over GF(2): bit j of row i = coefficient of x_j in y_i."""
+    a = [(1 << i) | (1 << ((i + 4) & 7)) | (1 << ((i + 5) & 7)) | (1 << ((i + 6) & 7)) | (1 << ((i + 7) & 7))
+         for i in range(8)]
+    m, inv = a[:], [1 << i for i in range(8)]
+    for col in range(8):
+        piv = next(r for r in range(col, 8) if (m[r] >> col) & 1)
+        m[col], m[piv] = m[piv], m[col]
+        inv[col], inv[piv] = inv[piv], inv[col]
+        for r in range(8):
+            if r != col and (m[r] >> col) & 1:
+                m[r] ^= m[col]
+                inv[r] ^= inv[col]
+    return inv
+
+
+class Net:
+    """A network of two-input gates over named primary inputs."""
+
+    def __init__(self, pis):
+        self.pis = list(pis)
+        self.gates = {}  # name -> (op, a, b)
+        self.order = []
+        self.outs = []
+
+    def gate(self, name, op, a, b):
+        assert name not in self.gates and name not in self.pis
+        self.gates[name] = (op, a, b)
+        self.order.append(name)
+        return name
+
+    def xor_chain(self, prefix, terms):
+        acc = terms[0]
+        for i, t in enumerate(terms[1:]):
+            acc = self.gate(f"{prefix}_{i}", "^", acc, t)
+        return acc
+
+    def add_circuit(self, tag, u):
+        """The S-box circuit on planes u[0..7] (u[0] = most significant bit); returns its 8 outputs."""
+        ren = {f"u{i}": u[i] for i in range(8)}
+        for out, op, a, b in circuit_gates():
+            ren[out] = self.gate(f"{tag}{out}", op, ren.get(a, a), ren.get(b, b))
+        return [ren[f"s{i}"] for i in range(8)]
+
+
+def encrypt_net():
+    """x[t] (bit t) -> S(x)[t] ^ k[t], the affine constant left to the round keys."""
+    net = Net([f"x{t}" for t in range(8)] + [f"k{t}" for t in range(8)])
+    o = net.add_circuit("c_", [f"x{7 - i}" for i in range(8)])
+    for t in range(8):
+        net.outs.append(net.gate(f"y{t}", "^", o[7 - t], f"k{t}"))
+    return net
+
+
+def decrypt_net():
+    """x[t] (input already XORed with the affine constant) -> A^-1 F(A^-1 x)[t] ^ k[t]."""
+    rows = affine_inverse_rows()
+    net = Net([f"x{t}" for t in range(8)] + [f"k{t}" for t in range(8)])
+    z = [net.xor_chain(f"z{i}", [f"x{j}" for j in range(8) if (rows[i] >> j) & 1]) for i in range(8)]
+    o = net.add_circuit("c_", [z[7 - i] for i in range(8)])
+    f = [o[7 - t] for t in range(8)]
+    for i in range(8):
+        terms = [f[j] for j in range(8) if (rows[i] >> j) & 1] + [f"k{i}"]
+        net.outs.append(net.xor_chain(f"y{i}", terms))
+    return net
+
+
+def map_lut3(net, passes=8):
+    """Cut-based mapping onto 3-input tables; returns {node: leaves} for the chosen cover."""
+    fanout = {}
+    for n in net.order:
+        for x in net.gates[n][1:]:
+            fanout[x] = fanout.get(x, 0) + 1
+    for o in net.outs:
+        fanout[o] = fanout.get(o, 0) + 1
+    cuts = {p: [frozenset([p])] for p in net.pis}
+    for n in net.order:
+        _, a, b = net.gates[n]
+        cs = sorted({c1 | c2 for c1 in cuts[a] for c2 in cuts[b] if len(c1 | c2) <= 3}, key=len)
+        keep = []
+        for c in cs:
+            if not any(k <= c for k in keep):
+                keep.append(c)
+        cuts[n] = keep + [frozenset([n])]
+
+    def choices(n):
+        return [c for c in cuts[n] if c != frozenset([n])]
+
+    flow = {p: 0.0 for p in net.pis}
+    best = {}
+    for n in net.order:
+        v, c = min(((1 + sum(flow[x] / max(1, fanout.get(x, 1)) for x in c), sorted(c)) for c in choices(n)))
+        flow[n], best[n] = v, frozenset(c)
+
+    def cover():
+        req, stack = set(), list(net.outs)
+        while stack:
+            n = stack.pop()
+            if n in net.pis or n in req:
+                continue
+            req.add(n)
+            stack.extend(best[n])
+        return req
+
+    def refs():
+        r = {}
+        for n in cover():
+            for x in best[n]:
+                r[x] = r.get(x, 0) + 1
+        for o in net.outs:
+            r[o] = r.get(o, 0) + 1
+        return r
+
+    def deref(n, r):
+        area = 1
+        for x in best[n]:
+            if x not in net.pis:
+                r[x] -= 1
+                if r[x] == 0:
+                    area += deref(x, r)
+        return area
+
+    def ref(n, r):
+        area = 1
+        for x in best[n]:
+            if x not in net.pis:
+                r[x] = r.get(x, 0) + 1
+                if r[x] == 1:
+                    area += ref(x, r)
+        return area
+
+    for _ in range(passes):
+        r = refs()
+        for n in net.order:
+            if r.get(n, 0) == 0:
+                continue
+            deref(n, r)
+            scored = []
+            for c in choices(n):
+                old, best[n] = best[n], c
+                scored.append((ref(n, r), sorted(c), c))
+                deref(n, r)
+                best[n] = old
+            best[n] = min(scored)[2]
+            ref(n, r)
+    return {n: sorted(best[n]) for n in cover()}
+
+
+def truth_table(net, node, leaves):
+    """lop3 immediate of node as a function of its cut's leaves, padded to three operands with the first."""
+    ops = (leaves + [leaves[0]] * 3)[:3]
+    imm = 0
+    for i in range(8):
+        assign = {}
+        for j, leaf in enumerate(ops):
+            bit = (i >> (2 - j)) & 1
+            if assign.setdefault(leaf, bit) != bit:
+                assign = None  # a combination the padding rules out: leave its bit 0
+                break
+        if assign is None:
+            continue
+        memo = dict(assign)
+
+        def ev(n):
+            if n not in memo:
+                op, a, b = net.gates[n]
+                memo[n] = (ev(a) & ev(b)) if op == "&" else (ev(a) ^ ev(b))
+            return memo[n]
+
+        imm |= ev(node) << i
+    return ops, imm
+
+
+def emit(net, cover, fname):
+    topo = [n for n in net.order if n in cover]
+    names = {f"x{t}": f"x[{t}]" for t in range(8)}
+    names.update({f"k{t}": f"k[{t}]" for t in range(8)})
+    lines = []
+    for i, n in enumerate(topo):
+        ops, imm = truth_table(net, n, cover[n])
+        names[n] = f"v{i}"
+        lines.append(f"    const uint32_t v{i} = lop({names[ops[0]]}, {names[ops[1]]}, {names[ops[2]]}, Tt<0x{imm:02x}>{{}});")
+    for t, o in enumerate(net.outs):
+        lines.append(f"    x[{t}] = {names[o]};")
+    head = (f"template <class Lop>\nGBAES_HD constexpr void {fname}(uint32_t* x, const uint32_t (&k)[8], "
+            f"const Lop& lop) {{  // {len(topo)} tables")
+    return head + "\n" + "\n".join(lines) + "\n}\n"
+
+
+def main():
+    enc, dec = encrypt_net(), decrypt_net()
+    enc_cover, dec_cover = map_lut3(enc), map_lut3(dec)
+    text = f"""// Generated by gen_sbox_lut3.py from sbox_circuit in bitsliced.h -- do not edit.
+//
+// The bitsliced S-box networks as three-input lookup tables (one LOP3 each on
+// the GPU): sbox_key_lut3 computes x[t] = S(x)[t] ^ k[t] without the affine
+// constant ({len(enc_cover)} tables for the {len(enc.gates)} two-input gates of the circuit plus the key
+// XORs); inv_sbox_key_lut3 computes x[t] = A^-1 F(A^-1 x)[t] ^ k[t] for input
+// already XORed with the affine constant ({len(dec_cover)} tables for {len(dec.gates)} gates).  Planes are
+// indexed by bit (x[0] = least significant).  lop(a, b, c, Tt<imm>) returns the
+// function whose truth table imm lists F(a, b, c) at bit 4a + 2b + c (the table
+// travels as a type, so that it stays a compile-time constant).
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#ifndef GBAES_HD
+#ifdef __CUDACC__
+#define GBAES_HD __host__ __device__
+#else
+#define GBAES_HD
+#endif
+#endif
+
+namespace gbaes {{
+namespace bs {{
+
+template <uint32_t V>
+using Tt = std::integral_constant<uint32_t, V>;
+
+{emit(enc, enc_cover, "sbox_key_lut3")}
+{emit(dec, dec_cover, "inv_sbox_key_lut3")}
+}}  // namespace bs
+}}  // namespace gbaes
+"""
+    with open(os.path.join(HERE, "sbox_lut3.h"), "w") as f:
+        f.write(text)
+    print(f"sbox_lut3.h: {len(enc_cover)} + {len(dec_cover)} tables")
+
+
+if __name__ == "__main__":
+    main()
