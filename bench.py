@@ -61,8 +61,8 @@ LOOKUPS_PER_CLK_PER_SM = 32  # 32 banks x 4 B: one conflict-free 32-bit lookup p
 ALU_LANES_PER_CLK_PER_SM = 64  # integer ALU pipe: 4 SM sub-partitions x 16 lanes
 # The bitsliced kernel's integer-ALU instructions per 16-byte block, (Nr, decrypt) -> lane-ops, counted by ncu
 # (ALU-pipe utilisation x 2 warp instructions per clock per SM x active cycles x SMs x 32 / blocks) in
-# profiles/bitsliced_kernel_ecb_64MiB_ncu_full.md.
-BITSLICED_ALU_OPS_PER_BLOCK = {(10, 0): 683.2, (10, 1): 826.9, (14, 0): 923.6, (14, 1): 1127.2}
+# profiles/bitsliced_kernel_ecb_256MiB_ncu_full.md.
+BITSLICED_ALU_OPS_PER_BLOCK = {(10, 0): 662.1, (10, 1): 810.1, (14, 0): 894.4, (14, 1): 1104.4}
 
 
 def parse_args():
