@@ -20,8 +20,9 @@ cover of its gates by three-input cones.  This script
      PTX's lop3 encoding (bit i = F(i >> 2 & 1, i >> 1 & 1, i & 1) for operands
      a, b, c), in the order the network computes them.
 
-Run from anywhere: python gen_sbox_lut3.py  (rewrites sbox_lut3.h next to it).
+Run from anywhere: python gen_sbox_lut3.py [--out PATH]  (default: rewrites sbox_lut3.h next to it).
 """
+import argparse
 import os
 import re
 
@@ -233,6 +234,9 @@ def emit(net, cover, fname):
 
 
 def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=os.path.join(HERE, "sbox_lut3.h"))
+    out = ap.parse_args().out
     enc, dec = encrypt_net(), decrypt_net()
     enc_cover, dec_cover = map_lut3(enc), map_lut3(dec)
     text = f"""// Generated by gen_sbox_lut3.py from sbox_circuit in bitsliced.h -- do not edit.
@@ -269,9 +273,9 @@ using Tt = std::integral_constant<uint32_t, V>;
 }}  // namespace bs
 }}  // namespace gbaes
 """
-    with open(os.path.join(HERE, "sbox_lut3.h"), "w") as f:
+    with open(out, "w") as f:
         f.write(text)
-    print(f"sbox_lut3.h: {len(enc_cover)} + {len(dec_cover)} tables")
+    print(f"{os.path.basename(out)}: {len(enc_cover)} + {len(dec_cover)} tables")
 
 
 if __name__ == "__main__":
