@@ -12,15 +12,26 @@ cover of its gates by three-input cones.  This script
      a round-key plane XORed onto each output bit (encryption), and the inverse
      S-box A^-1 F(A^-1 x) with the same key XOR (decryption; A^-1 the inverse of
      the S-box's affine matrix, F the circuit),
-  3. maps each network onto three-input lookup tables: every 3-feasible cut of
+  3. re-brackets the XOR sums the circuit computes once (maximal trees of XOR
+     gates whose inner results feed nothing else: any bracketing of the same
+     terms gives the same sum), each tree as recorded in SHAPES below,
+  4. maps each network onto three-input lookup tables: every 3-feasible cut of
      every gate is enumerated, each gate takes the cut of least area flow, and
      passes of exact-area recovery then re-choose cuts where that frees the most
      tables (the standard cut-based technology-mapping method of FPGA tools),
-  4. emits each table as one `lop(a, b, c, truth_table)` call, the truth table in
+  5. emits each table as one `lop(a, b, c, truth_table)` call, the truth table in
      PTX's lop3 encoding (bit i = F(i >> 2 & 1, i >> 1 & 1, i & 1) for operands
      a, b, c), in the order the network computes them.
 
-Run from anywhere: python gen_sbox_lut3.py [--out PATH]  (default: rewrites sbox_lut3.h next to it).
+The bracketings in SHAPES come from `--search`: a hill climb that re-draws one
+tree's bracketing at a time and keeps the draw when the mapped table count does
+not grow (encryption 91 -> 81 tables, decryption 110 -> 102 from the circuit's
+own bracketing).  A tree's entry seeds the splitmix64 generator that picks
+which two of its remaining terms to XOR next; trees without an entry keep the
+circuit's bracketing.
+
+Run from anywhere: python gen_sbox_lut3.py [--out PATH]  (default: rewrites sbox_lut3.h next to it);
+python gen_sbox_lut3.py --search enc|dec [--iters N] [--seed S] prints a new SHAPES entry.
 """
 import argparse
 import os
@@ -109,6 +120,95 @@ def decrypt_net():
         terms = [f[j] for j in range(8) if (rows[i] >> j) & 1] + [f"k{i}"]
         net.outs.append(net.xor_chain(f"y{i}", terms))
     return net
+
+
+class SplitMix64:
+    """The splitmix64 generator (Steele, Lea, Flood 2014): a 64-bit state stepped by a constant, mixed."""
+
+    def __init__(self, seed):
+        self.state = seed & (2 ** 64 - 1)
+
+    def next(self):
+        self.state = (self.state + 0x9E3779B97F4A7C15) & (2 ** 64 - 1)
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & (2 ** 64 - 1)
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & (2 ** 64 - 1)
+        return z ^ (z >> 31)
+
+    def below(self, n):
+        return self.next() % n
+
+
+def xor_trees(net):
+    """{root: terms} for each maximal tree of XOR gates whose inner nodes feed only the tree (> 2 terms)."""
+    fanout = {}
+    for n in net.order:
+        for x in net.gates[n][1:]:
+            fanout[x] = fanout.get(x, 0) + 1
+    for o in net.outs:
+        fanout[o] = fanout.get(o, 0) + 1
+    inner = {x for n in net.order if net.gates[n][0] == "^" for x in net.gates[n][1:]
+             if x in net.gates and net.gates[x][0] == "^" and fanout[x] == 1}
+
+    def terms(n):
+        out = []
+        for x in net.gates[n][1:]:
+            out += terms(x) if x in inner else [x]
+        return out
+
+    trees = {n: terms(n) for n in net.order if net.gates[n][0] == "^" and n not in inner}
+    return {r: t for r, t in trees.items() if len(t) > 2}
+
+
+def reshape(net, shapes):
+    """A copy of net with the XOR trees named in shapes re-bracketed by their seeds."""
+    trees = xor_trees(net)
+    new = Net(net.pis)
+    done, count = {}, [0]
+
+    def build(n):
+        if n in net.pis:
+            return n
+        if n not in done:
+            op, a, b = net.gates[n]
+            if n in trees and shapes.get(n):
+                terms = [build(x) for x in trees[n]]
+                rng = SplitMix64(shapes[n])
+                while len(terms) > 2:
+                    i = rng.below(len(terms))
+                    j = rng.below(len(terms) - 1)
+                    j += j >= i
+                    count[0] += 1
+                    g = new.gate(f"{n}__{count[0]}", "^", terms[i], terms[j])
+                    terms = [x for m, x in enumerate(terms) if m not in (i, j)] + [g]
+                done[n] = new.gate(n, "^", terms[0], terms[1])
+            else:
+                done[n] = new.gate(n, op, build(a), build(b))
+        return done[n]
+
+    for o in net.outs:
+        build(o)
+    new.outs = [done[o] for o in net.outs]
+    return new
+
+
+def search(net, iters, seed):
+    """Hill climb over the trees' bracketings; returns the shapes of the best network found."""
+    roots = sorted(xor_trees(net))
+    rng, shapes = SplitMix64(seed), {}
+    cur = len(map_lut3(reshape(net, shapes), passes=3))
+    for _ in range(iters):
+        r = roots[rng.below(len(roots))]
+        old = shapes.get(r)
+        shapes[r] = rng.next() | 1
+        c = len(map_lut3(reshape(net, shapes), passes=3))
+        if c <= cur:
+            cur = c
+        elif old is None:
+            del shapes[r]
+        else:
+            shapes[r] = old
+    return shapes
 
 
 def map_lut3(net, passes=8):
@@ -233,11 +333,79 @@ def emit(net, cover, fname):
     return head + "\n" + "\n".join(lines) + "\n}\n"
 
 
+# Bracketings found by --search (seed 1, 1,500 steps each): tree root -> splitmix64 seed.
+SHAPES = {
+    "enc": {
+        "c_l6": 8411996437093593279,
+        "c_m20": 6036339614689729693,
+        "c_m21": 2927808880244328445,
+        "c_m22": 12944380480760822807,
+        "c_m23": 14618154987885078747,
+        "c_m38": 2243067523905852675,
+        "c_m40": 961137476199508239,
+        "c_t19": 5039539338173171385,
+        "c_t22": 1163728296864529161,
+        "y0": 13290268570847108467,
+        "y1": 15053352997926904907,
+        "y2": 17407377188203331605,
+        "y3": 11924832088314853027,
+        "y4": 4621030392246333243,
+        "y5": 15563214200757333989,
+        "y6": 65468312225334051,
+        "y7": 5208041666417506291,
+    },
+    "dec": {
+        "c_l6": 15053352997926904907,
+        "c_m20": 17208915671098355703,
+        "c_m21": 7467859444893362743,
+        "c_m22": 10174854292179124725,
+        "c_m23": 13900687464464979805,
+        "c_m38": 2243067523905852675,
+        "c_m40": 6572600082127798947,
+        "c_s0": 7589964776984157073,
+        "c_s1": 12327957813683028421,
+        "c_s2": 14618154987885078747,
+        "c_s3": 2037386553481293547,
+        "c_s4": 13290268570847108467,
+        "c_s5": 17508866225838119887,
+        "c_s6": 13993476446138047205,
+        "c_s7": 15305350299310617173,
+        "c_t19": 5208041666417506291,
+        "c_t22": 12677037431724280505,
+        "c_t5": 3078487764655139347,
+        "y0_2": 3836897347045491961,
+        "y1_2": 17537885973340814571,
+        "y2_2": 15563214200757333989,
+        "y3_2": 961137476199508239,
+        "y4_2": 1536169924725109803,
+        "y5_2": 7880484762772585691,
+        "y6_2": 7710113369677980097,
+        "y7_2": 1501121449731526029,
+        "z0_1": 12944380480760822807,
+        "z1_1": 15459438588758570425,
+        "z2_1": 12110998379208263153,
+        "z4_1": 14080516419620970537,
+        "z5_1": 6682256367785181475,
+        "z6_1": 15587678707349028255,
+        "z7_1": 17978135531838172359,
+    },
+}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=os.path.join(HERE, "sbox_lut3.h"))
-    out = ap.parse_args().out
-    enc, dec = encrypt_net(), decrypt_net()
+    ap.add_argument("--search", choices=("enc", "dec"))
+    ap.add_argument("--iters", type=int, default=1500)
+    ap.add_argument("--seed", type=int, default=1)
+    args = ap.parse_args()
+    if args.search:
+        net = encrypt_net() if args.search == "enc" else decrypt_net()
+        shapes = search(net, args.iters, args.seed)
+        print(len(map_lut3(reshape(net, shapes))), "tables;", dict(sorted(shapes.items())))
+        return
+    out = args.out
+    enc, dec = reshape(encrypt_net(), SHAPES["enc"]), reshape(decrypt_net(), SHAPES["dec"])
     enc_cover, dec_cover = map_lut3(enc), map_lut3(dec)
     text = f"""// Generated by gen_sbox_lut3.py from sbox_circuit in bitsliced.h -- do not edit.
 //
