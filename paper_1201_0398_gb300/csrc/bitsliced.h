@@ -19,9 +19,8 @@
 //    y is inv(A^-1 (y ^ 0x63)) = A^-1 F(A^-1 (y ^ 0x63)), the XOR with 0x63
 //    again folded into the round keys; A^-1 costs one three-input XOR per bit.
 //  * ShiftRows is a renaming of planes (across the two halves of a split state,
-//    see "half states" below); MixColumns and AddRoundKey are XORs;
-//    InvMixColumns is MixColumns after the preprocessing
-//    a0 ^= 4(a0^a2), a2 ^= 4(a0^a2), a1 ^= 4(a1^a3), a3 ^= 4(a1^a3).
+//    see "half states" below); MixColumns, InvMixColumns and AddRoundKey are
+//    XORs (the column maps as generated XOR programs, sbox_lut3.h).
 //
 // The circuit is checked exhaustively at compile time against the S-box of
 // aes_tables.h (static_asserts below).  Everything here is plain C++ usable on
@@ -267,17 +266,33 @@ constexpr bool check_sbox_lut3() {
 }
 static_assert(check_sbox_lut3(), "the table-mapped S-box networks do not reproduce the S-box");
 
-// Multiplication by {02} on one byte's planes (t[0] = least significant bit).
-GBAES_HD inline void xtime_planes(const uint32_t* a, uint32_t* y) {
-    y[0] = a[7];
-    y[1] = a[0] ^ a[7];
-    y[2] = a[1];
-    y[3] = a[2] ^ a[7];
-    y[4] = a[3] ^ a[7];
-    y[5] = a[4];
-    y[6] = a[5];
-    y[7] = a[6];
+// MixColumns and InvMixColumns programs against the column maps written out with
+// GF(2^8) products, on all 32 unit columns at once (plane i holds unit column i in
+// bit i; the maps are linear, so the unit columns decide them).
+constexpr bool check_mix_lut3() {
+    constexpr uint8_t kMix[4] = {2, 3, 1, 1}, kInv[4] = {14, 11, 13, 9};
+    uint32_t m[32] = {}, v[32] = {};
+    for (int i = 0; i < 32; ++i) m[i] = v[i] = 1u << i;
+    mix_column_lut3(m, Lop3Eval{});
+    inv_mix_column_lut3(v, Lop3Eval{});
+    for (int i = 0; i < 32; ++i) {
+        uint8_t a[4] = {};
+        a[i / 8] = (uint8_t)(1u << (i % 8));
+        for (int q = 0; q < 4; ++q) {
+            uint8_t want_m = 0, want_v = 0;
+            for (int j = 0; j < 4; ++j) {
+                want_m ^= gf_mul_log(kMix[j], a[(q + j) & 3]);
+                want_v ^= gf_mul_log(kInv[j], a[(q + j) & 3]);
+            }
+            for (int t = 0; t < 8; ++t) {
+                if (((m[8 * q + t] >> i) & 1u) != ((want_m >> t) & 1u)) return false;
+                if (((v[8 * q + t] >> i) & 1u) != ((want_v >> t) & 1u)) return false;
+            }
+        }
+    }
+    return true;
 }
+static_assert(check_mix_lut3(), "the MixColumns / InvMixColumns programs do not reproduce the column maps");
 
 // Byte permute: byte i of the result is byte (sel >> 4i) & 7 of the eight
 // bytes {a (bytes 0-3), b (bytes 4-7)}; PRMT on the device.
@@ -404,77 +419,18 @@ GBAES_HD inline void add_key_half(uint32_t (&s)[64], const Keys& keys, int r) {
     }
 }
 
-// MixColumns on the half's two columns (after ShiftRows and SubBytes):
-// out_q = 2a_q + 3a_{q+1} + a_{q+2} + a_{q+3} = xtime(t_q) + t_{q+1} + a_{q+3},
-// t_q = a_q + a_{q+1}.  The round key was added before it, transformed (see
-// make_key_planes).
+// MixColumns on the half's two columns (after ShiftRows and SubBytes), each as a
+// generated program of two- and three-input XORs (sbox_lut3.h).  The round key
+// was added before it, transformed (see make_key_planes).
 GBAES_HD inline void mix_half(uint32_t (&s)[64]) {
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        uint32_t* a[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) a[q] = &s[8 * (4 * c + q)];
-        uint32_t tt[4][8], n[4][8];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int t = 0; t < 8; ++t) tt[q][t] = a[q][t] ^ a[(q + 1) & 3][t];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint32_t x2[8];
-            xtime_planes(tt[q], x2);
-#pragma unroll
-            for (int t = 0; t < 8; ++t) n[q][t] = x2[t] ^ tt[(q + 1) & 3][t] ^ a[(q + 3) & 3][t];
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int t = 0; t < 8; ++t) a[q][t] = n[q][t];
-    }
+    mix_column_lut3(&s[0], Lop3{});
+    mix_column_lut3(&s[32], Lop3{});
 }
 
-// InvMixColumns (MixColumns after the {04} preprocessing a0 ^= 4(a0^a2),
-// a2 ^= 4(a0^a2), a1 ^= 4(a1^a3), a3 ^= 4(a1^a3)) on the half's two columns.
+// InvMixColumns on the half's two columns, each as a generated XOR program.
 GBAES_HD inline void inv_mix_half(uint32_t (&s)[64]) {
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        uint32_t* a[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) a[q] = &s[8 * (4 * c + q)];
-        uint32_t e[8], e2[8], u4[8], o[8], o2[8], v4[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            e[t] = a[0][t] ^ a[2][t];
-            o[t] = a[1][t] ^ a[3][t];
-        }
-        xtime_planes(e, e2);
-        xtime_planes(e2, u4);
-        xtime_planes(o, o2);
-        xtime_planes(o2, v4);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            a[0][t] ^= u4[t];
-            a[2][t] ^= u4[t];
-            a[1][t] ^= v4[t];
-            a[3][t] ^= v4[t];
-        }
-        uint32_t tt[4][8], n[4][8];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int t = 0; t < 8; ++t) tt[q][t] = a[q][t] ^ a[(q + 1) & 3][t];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint32_t x2[8];
-            xtime_planes(tt[q], x2);
-#pragma unroll
-            for (int t = 0; t < 8; ++t) n[q][t] = x2[t] ^ tt[(q + 1) & 3][t] ^ a[(q + 3) & 3][t];
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int t = 0; t < 8; ++t) a[q][t] = n[q][t];
-    }
+    inv_mix_column_lut3(&s[0], Lop3{});
+    inv_mix_column_lut3(&s[32], Lop3{});
 }
 
 // SubBytes with the key planes of step r added to its output, on a half.

@@ -34,6 +34,7 @@ Run from anywhere: python gen_sbox_lut3.py [--out PATH]  (default: rewrites sbox
 python gen_sbox_lut3.py --search enc|dec [--iters N] [--seed S] prints a new SHAPES entry.
 """
 import argparse
+import itertools
 import os
 import re
 
@@ -333,6 +334,112 @@ def emit(net, cover, fname):
     return head + "\n" + "\n".join(lines) + "\n}\n"
 
 
+# ------------------------------------------------------- MixColumns as XOR programs
+
+
+def gf_mul(a, b):
+    """Product in GF(2^8) modulo x^8 + x^4 + x^3 + x + 1."""
+    r = 0
+    for i in range(8):
+        if (b >> i) & 1:
+            r ^= a << i
+    for i in range(15, 7, -1):
+        if (r >> i) & 1:
+            r ^= 0x11B << (i - 8)
+    return r
+
+
+def column_rows(coef):
+    """The 32x32 GF(2) matrix of a column map out_q = sum_j coef[j] a_{q+j}: row 8q+t (output byte q,
+    bit t) as a bit mask over input bit 8q'+t' (byte q', bit t')."""
+    rows = []
+    for q in range(4):
+        for t in range(8):
+            m = 0
+            for j, c in enumerate(coef):
+                for tp in range(8):
+                    if (gf_mul(c, 1 << tp) >> t) & 1:
+                        m |= 1 << (8 * ((q + j) % 4) + tp)
+            rows.append(m)
+    return rows
+
+
+def xor_program(rows, seed):
+    """A straight-line program of XORs of two or three signals computing every row (greedy: repeatedly
+    create the sum of the pair or triple of signals that lowers the three-input-gate cost of the
+    remaining rows most, a seeded jitter breaking ties).  Returns (steps, rows as signal sets); step k
+    creates signal 32 + k as the XOR of its operands."""
+    rng = SplitMix64(seed)
+    rows_s = [set(i for i in range(32) if (r >> i) & 1) for r in rows]
+
+    def cost(k):
+        return k // 2 if k > 1 else 0  # three-input gates to sum k signals: ceil((k - 1) / 2)
+
+    steps = []
+    while True:
+        cands = set()
+        for rs in rows_s:
+            if len(rs) > 1:
+                srt = sorted(rs)
+                cands.update(itertools.combinations(srt, 2))
+                cands.update(itertools.combinations(srt, 3))
+        best, best_v = None, 0.0
+        for c in sorted(cands):
+            gain = sum(cost(len(rs)) - cost(len(rs) - len(c) + 1) for rs in rows_s
+                       if len(rs) > 1 and all(x in rs for x in c))
+            v = gain - 1 + (rng.next() >> 11) / float(1 << 53) * 0.5
+            if v > best_v:
+                best, best_v = c, v
+        if best is None:
+            break
+        new = 32 + len(steps)
+        steps.append(best)
+        for rs in rows_s:
+            if len(rs) > 1 and all(x in rs for x in best):
+                rs.difference_update(best)
+                rs.add(new)
+    return steps, rows_s
+
+
+def emit_linear(fname, what, steps, rows_s):
+    """The program as lop calls on 32 planes in place (x[8q + t] = bit t of byte q of the column)."""
+    names = {i: f"x[{i}]" for i in range(32)}
+    lines = [f"    const uint32_t i{i} = x[{i}];" for i in range(32)]
+    names = {i: f"i{i}" for i in range(32)}
+    xor2, xor3 = 0x3C, 0x96  # a ^ b (third operand repeats a), a ^ b ^ c
+    n = 0
+
+    def lop(ops):
+        nonlocal n
+        v = f"w{n}"
+        n += 1
+        if len(ops) == 2:
+            lines.append(f"    const uint32_t {v} = lop({ops[0]}, {ops[1]}, {ops[0]}, Tt<0x{xor2:02x}>{{}});")
+        else:
+            lines.append(f"    const uint32_t {v} = lop({ops[0]}, {ops[1]}, {ops[2]}, Tt<0x{xor3:02x}>{{}});")
+        return v
+
+    for k, ops in enumerate(steps):
+        names[32 + k] = lop([names[o] for o in ops])
+    outs = []
+    for rs in rows_s:
+        terms = [names[o] for o in sorted(rs)]
+        while len(terms) > 1:
+            take = terms[:3]
+            terms = [lop(take)] + terms[3:]
+        outs.append(terms[0])
+    lines += [f"    x[{i}] = {o};" for i, o in enumerate(outs)]
+    head = (f"// {what}\ntemplate <class Lop>\nGBAES_HD constexpr void {fname}(uint32_t* x, const Lop& lop) {{  "
+            f"// {n} tables")
+    return head + "\n" + "\n".join(lines) + "\n}\n", n
+
+
+# The column maps: MixColumns (02 03 01 01) and InvMixColumns (0e 0b 0d 09), as coefficient rows.
+MIX_COEF = {"mix": (2, 3, 1, 1), "inv_mix": (14, 11, 13, 9)}
+# Seeds of the greedy XOR programs, chosen by --search-mix (the program with the fewest gates of 64 seeds).
+MIX_SEEDS = {"mix": 8, "inv_mix": 57}
+
+
 # Bracketings found by --search (seed 1, 1,500 steps each): tree root -> splitmix64 seed.
 SHAPES = {
     "enc": {
@@ -396,9 +503,18 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=os.path.join(HERE, "sbox_lut3.h"))
     ap.add_argument("--search", choices=("enc", "dec"))
+    ap.add_argument("--search-mix", choices=tuple(MIX_COEF))
     ap.add_argument("--iters", type=int, default=1500)
     ap.add_argument("--seed", type=int, default=1)
     args = ap.parse_args()
+    if args.search_mix:
+        rows = column_rows(MIX_COEF[args.search_mix])
+        counts = []
+        for sd in range(args.seed, args.seed + 64):
+            steps, rows_s = xor_program(rows, sd)
+            counts.append((len(steps) + sum(len(r) // 2 for r in rows_s if len(r) > 1), sd))
+        print("fewest gates, seed:", min(counts))
+        return
     if args.search:
         net = encrypt_net() if args.search == "enc" else decrypt_net()
         shapes = search(net, args.iters, args.seed)
@@ -407,6 +523,12 @@ def main():
     out = args.out
     enc, dec = reshape(encrypt_net(), SHAPES["enc"]), reshape(decrypt_net(), SHAPES["dec"])
     enc_cover, dec_cover = map_lut3(enc), map_lut3(dec)
+    mix_code, mix_n = emit_linear(
+        "mix_column_lut3", "MixColumns of one column in place: out_q = 02 a_q + 03 a_q+1 + a_q+2 + a_q+3.",
+        *xor_program(column_rows(MIX_COEF["mix"]), MIX_SEEDS["mix"]))
+    inv_code, inv_n = emit_linear(
+        "inv_mix_column_lut3", "InvMixColumns of one column in place: out_q = 0e a_q + 0b a_q+1 + 0d a_q+2 + 09 a_q+3.",
+        *xor_program(column_rows(MIX_COEF["inv_mix"]), MIX_SEEDS["inv_mix"]))
     text = f"""// Generated by gen_sbox_lut3.py from sbox_circuit in bitsliced.h -- do not edit.
 //
 // The bitsliced S-box networks as three-input lookup tables (one LOP3 each on
@@ -414,7 +536,10 @@ def main():
 // constant ({len(enc_cover)} tables for the {len(enc.gates)} two-input gates of the circuit plus the key
 // XORs); inv_sbox_key_lut3 computes x[t] = A^-1 F(A^-1 x)[t] ^ k[t] for input
 // already XORed with the affine constant ({len(dec_cover)} tables for {len(dec.gates)} gates).  Planes are
-// indexed by bit (x[0] = least significant).  lop(a, b, c, Tt<imm>) returns the
+// indexed by bit (x[0] = least significant).  mix_column_lut3 and
+// inv_mix_column_lut3 compute MixColumns ({mix_n} tables) and InvMixColumns ({inv_n}) on
+// the 32 planes of one state column (x[8q + t] = bit t of row q) as greedy
+// programs of two- and three-input XORs.  lop(a, b, c, Tt<imm>) returns the
 // function whose truth table imm lists F(a, b, c) at bit 4a + 2b + c (the table
 // travels as a type, so that it stays a compile-time constant).
 #pragma once
@@ -438,12 +563,14 @@ using Tt = std::integral_constant<uint32_t, V>;
 
 {emit(enc, enc_cover, "sbox_key_lut3")}
 {emit(dec, dec_cover, "inv_sbox_key_lut3")}
+{mix_code}
+{inv_code}
 }}  // namespace bs
 }}  // namespace gbaes
 """
     with open(out, "w") as f:
         f.write(text)
-    print(f"{os.path.basename(out)}: {len(enc_cover)} + {len(dec_cover)} tables")
+    print(f"{os.path.basename(out)}: {len(enc_cover)} + {len(dec_cover)} tables, mix {mix_n} + {inv_n}")
 
 
 if __name__ == "__main__":
