@@ -1,4 +1,5 @@
-"""Writes sbox_lut3.h: the bitsliced S-box circuits mapped onto three-input lookup tables.
+"""Writes sbox_lut3.h: the bitsliced S-box circuits mapped onto three-input lookup tables,
+and MixColumns / InvMixColumns as programs of two- and three-input XORs.
 
 The bitsliced kernel spends most of its integer-ALU instructions in the S-box
 circuit (bitsliced.h, `sbox_circuit`: Boyar and Peralta's depth-16 circuit, 34
@@ -23,6 +24,16 @@ cover of its gates by three-input cones.  This script
      PTX's lop3 encoding (bit i = F(i >> 2 & 1, i >> 1 & 1, i & 1) for operands
      a, b, c), in the order the network computes them.
 
+The column maps (the 32x32 GF(2) matrices of MixColumns and InvMixColumns over
+a column's 32 bit planes) are written as straight-line programs by a greedy
+method in the manner of Paar's (1997) common-subexpression algorithm, adapted
+to three-input gates: while some output still needs more than one gate, create
+the XOR of the pair or triple of available signals whose creation lowers the
+remaining three-input-gate count most, ties broken by a seeded jitter; each
+output then sums its remaining signals three at a time.  MIX_SEEDS records the
+jitter seed with the fewest gates among 64 (`--search-mix`): MixColumns 56
+tables per column, InvMixColumns 101 (the kernel's xtime forms took 76 and 118).
+
 The bracketings in SHAPES come from `--search`: a hill climb that re-draws one
 tree's bracketing at a time and keeps the draw when the mapped table count does
 not grow (encryption 91 -> 81 tables, decryption 110 -> 102 from the circuit's
@@ -31,7 +42,8 @@ which two of its remaining terms to XOR next; trees without an entry keep the
 circuit's bracketing.
 
 Run from anywhere: python gen_sbox_lut3.py [--out PATH]  (default: rewrites sbox_lut3.h next to it);
-python gen_sbox_lut3.py --search enc|dec [--iters N] [--seed S] prints a new SHAPES entry.
+python gen_sbox_lut3.py --search enc|dec [--iters N] [--seed S] prints a new SHAPES entry;
+python gen_sbox_lut3.py --search-mix mix|inv_mix [--seed S] prints the best of 64 seeds from S.
 """
 import argparse
 import itertools
