@@ -98,6 +98,8 @@ def parse_args():
                    help="--serve-sweep: take completions every this many ms during the replay (0: at the end)")
     p.add_argument("--serve-pin", action="store_true",
                    help="--serve-sweep: pin the server's scheduler and replay threads to their own CPUs")
+    p.add_argument("--serve-host", action="store_true",
+                   help="--serve-sweep: request payloads in page-locked host memory (1 GiB in-flight budget)")
     p.add_argument("--serve-sweep-shape", default="",
                    help="--serve-sweep: resident tile shape THREADSxBLOCKS_PER_THREAD (default 512x2)")
     p.add_argument("--profile-case", choices=PROFILE_CASES,
@@ -804,12 +806,14 @@ def run_serve_sweep(args):
         for resident in (m == "resident" for m in modes):
             shape = dict(threads=threads, blocks_per_thread=bpt) if resident else {}
             r = serving.run(rate=rate, duration_s=args.serve_sweep_seconds, check_last=200, resident=resident,
-                            pin_threads=args.serve_pin, poll_every_s=args.serve_poll_ms / 1e3, **shape)
+                            pin_threads=args.serve_pin, poll_every_s=args.serve_poll_ms / 1e3,
+                            host_payloads=args.serve_host, **({"budget_bytes": GiB} if args.serve_host else {}),
+                            **shape)
             torch.cuda.empty_cache()
             keep = ("mode", "value", "offered_gbs", "requests", "completed_ok", "p50_ms", "p99_ms", "p999_ms",
                     "max_ms", "p50_queue_ms", "p50_service_ms", "max_queue", "max_inflight_bytes", "shape",
                     "mismatches", "mean_batch_msgs", "p50_service_ms", "p99_service_ms", "host_threads",
-                    "kernel_launches")
+                    "kernel_launches", "payloads")
             print(json.dumps({"sweep": "serving", "rate": rate, "seconds": args.serve_sweep_seconds,
                               **{k: r[k] for k in keep if k in r}}), flush=True)
 

@@ -1,7 +1,7 @@
 """Open-loop serving run: Poisson arrivals replayed into the native server.
 
-Requests read slices of one device-resident input pool and write to an output
-ring.  Consecutive requests take consecutive ring space; the ring is larger
+Requests read slices of one input pool and write to an output ring, both in
+device memory (or both in page-locked host memory: host_payloads).  Consecutive requests take consecutive ring space; the ring is larger
 than the output bytes the budget lets be in flight (half the budget) plus the
 largest request, so two requests that are in flight together never share
 output bytes.  Latency is completion minus *scheduled* arrival.
@@ -18,7 +18,11 @@ GiB = 1 << 30
 def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8 << 30, nkeys: int = 1024,
         nstreams: int = 4, threads: int = 0, blocks_per_thread: int = 0, max_batch_msgs: int = 4096,
         pool_bytes: int = GiB, check_last: int = 1000, seed: int = workloads.SEED_SERVE,
-        resident: bool = False, pin_threads: bool = False, poll_every_s: float = 0.0) -> dict:
+        resident: bool = False, pin_threads: bool = False, poll_every_s: float = 0.0,
+        host_payloads: bool = False) -> dict:
+    """host_payloads: the input pool and the output ring live in page-locked host
+    memory instead of device memory (the kernels read and write them over the host
+    link); the ring then holds twice the in-flight budget, at least 1 GiB."""
     import torch
 
     w = workloads.serve_workload(rate=rate, duration_s=duration_s, nkeys=nkeys, seed=seed)
@@ -27,9 +31,13 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
     dev = torch.device("cuda")
     x = workloads.device_bytes(seed, pool_bytes, device=dev)
     max_len = int(w.lengths.max())
-    ring = max(2 * (budget_bytes // 2), 4 * GiB) + 2 * max_len
+    ring = max(2 * (budget_bytes // 2), GiB if host_payloads else 4 * GiB) + 2 * max_len
     ring = (ring + 15) // 16 * 16
-    y = torch.empty(ring + max_len, dtype=torch.uint8, device=dev)
+    if host_payloads:
+        x = x.cpu().pin_memory()
+        y = torch.empty(ring + max_len, dtype=torch.uint8, pin_memory=True)
+    else:
+        y = torch.empty(ring + max_len, dtype=torch.uint8, device=dev)
     rng = np.random.default_rng(seed + 1)
     in_off = rng.integers(0, (pool_bytes - w.lengths) // 16 + 1) * 16
     cum = np.concatenate([[0], np.cumsum(w.lengths)[:-1]])
@@ -91,6 +99,8 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
     mismatches = 0
     idx = np.arange(max(0, n - check_last), n)
     alone = torch.empty(int(w.lengths[idx].max()), dtype=torch.uint8, device=dev)
+    if host_payloads:
+        alone = alone.cpu().pin_memory()
     for i in idx:
         a, b, m = int(in_off[i]), int(out_off[i]), int(w.lengths[i])
         ecb_ex(keys[int(w.key_index[i])], x[a:a + m], alone[:m], decrypt=bool(w.decrypt[i]))
@@ -99,6 +109,7 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
     batches = np.unique(done["launch_s"])
     return {
         "mode": "resident kernel" if resident else "launch per micro-batch",
+        "payloads": "page-locked host memory" if host_payloads else "device memory",
         "value": total / span / 1e9, "unit": "GB/s", "requests": int(n), "completed_ok": int(ok.sum()),
         "offered_gbs": total / duration_s / 1e9, "bytes": total,
         "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),

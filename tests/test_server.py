@@ -567,3 +567,45 @@ def test_dryrun_unpinned_threads_report_no_cpu(gbaes):
     d = srv.diag()
     srv.close()
     assert d["sched_cpu"] == -1 and d["producer_cpu"] == -1
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("resident", (False, True))
+def test_server_with_payloads_in_page_locked_host_memory(gbaes, resident):
+    """Requests whose inputs and outputs live in page-locked host memory (the
+    kernels read and write them over the host link): both server modes, every
+    request against the oracle."""
+    rng = np.random.default_rng(77 + int(resident))
+    nkeys = 16
+    bits = rng.choice([128, 192, 256], nkeys)
+    raw_keys = [rng.integers(0, 256, b // 8, dtype=np.uint8).tobytes() for b in bits]
+    keys = [gbaes.Key(k) for k in raw_keys]
+    n = 2000
+    lengths = np.maximum((np.exp(rng.uniform(np.log(64), np.log(256 << 10), n)) // 16 * 16).astype(np.int64), 16)
+    pool = 8 << 20
+    x = torch.from_numpy(rng.integers(0, 256, pool, dtype=np.uint8)).pin_memory()
+    y = torch.zeros(int(lengths.sum()), dtype=torch.uint8).pin_memory()
+    in_off = (rng.integers(0, (pool - lengths) // 16 + 1) * 16).astype(np.int64)
+    out_off = np.concatenate([[0], np.cumsum(lengths)[:-1]])
+    reqs = np.zeros(n, gbaes.REQUEST)
+    reqs["id"] = np.arange(n)
+    reqs["in_ptr"] = x.data_ptr() + in_off
+    reqs["out_ptr"] = y.data_ptr() + out_off
+    reqs["nblocks"] = lengths // 16
+    reqs["key_index"] = rng.integers(0, nkeys, n)
+    reqs["decrypt"] = rng.integers(0, 2, n)
+    reqs["arrival_s"] = np.cumsum(rng.exponential(1.0 / 50_000.0, n))
+    srv = gbaes.Server(keys, resident=resident, threads=512, blocks_per_thread=2)
+    srv.replay(reqs)
+    srv.replay_join()
+    srv.drain(60.0)
+    done = srv.poll_all()
+    srv.close()
+    assert len(done) == n and (done["status"] == 0).all()
+    xs, ys = x.numpy(), y.numpy()
+    for i in range(n):
+        a, b, m = int(in_off[i]), int(out_off[i]), int(lengths[i])
+        k = int(reqs["key_index"][i])
+        want = oracle.ecb(raw_keys[k], int(bits[k]), xs[a:a + m], decrypt=bool(reqs["decrypt"][i]), nthreads=1)
+        assert np.array_equal(ys[b:b + m], want), i
+    assert gbaes.device_status() == 0
