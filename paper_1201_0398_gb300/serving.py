@@ -104,6 +104,8 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
     for i in idx:
         a, b, m = int(in_off[i]), int(out_off[i]), int(w.lengths[i])
         ecb_ex(keys[int(w.key_index[i])], x[a:a + m], alone[:m], decrypt=bool(w.decrypt[i]))
+        if host_payloads:
+            torch.cuda.synchronize()  # (host tensors: the comparison below does not wait for the stream)
         if not torch.equal(alone[:m], y[b:b + m]):
             mismatches += 1
     batches = np.unique(done["launch_s"])
