@@ -186,12 +186,6 @@ struct Lop3 {
 // (sbox_lut3.h), the key riding on its last tables.
 GBAES_HD inline void sbox_planes_key(uint32_t* x, const uint32_t (&k)[8]) { sbox_key_lut3(x, k, Lop3{}); }
 
-// Inverse S-box then XOR with 8 key planes, in place, for input already XORed
-// with the affine constant: A^-1 F(A^-1 x) ^ k as three-input tables.
-GBAES_HD inline void inv_sbox_planes_key(uint32_t* x, const uint32_t (&k)[8]) {
-    inv_sbox_key_lut3(x, k, Lop3{});
-}
-
 // Inverse S-box for input already XORed with the affine constant, in place:
 // A^-1 F(A^-1 x), F the circuit.
 GBAES_HD constexpr void inv_sbox_planes(uint32_t* x) {
@@ -236,63 +230,76 @@ constexpr bool check_sbox_circuit() {
 }
 static_assert(check_sbox_circuit(), "the S-box circuit does not reproduce the S-box");
 
-// The same, exhaustively, for the table-mapped networks the kernel runs, with all-zero
-// and all-one key planes: S(x) ^ key and S^-1(x) ^ key.
+// The same, exhaustively, for the table-mapped network the kernel runs, with all-zero
+// and all-one key planes: F(x) ^ key, F the S-box without its constant.
 constexpr bool check_sbox_lut3() {
     for (int key = 0; key < 256; key += 255)
         for (int g = 0; g < 8; ++g) {
-            uint32_t fwd[8] = {}, inv[8] = {}, kp[8] = {};
+            uint32_t fwd[8] = {}, kp[8] = {};
             for (int t = 0; t < 8; ++t) {
                 kp[t] = ((key >> t) & 1) ? 0xffffffffu : 0u;
-                for (int k = 0; k < 32; ++k) {
-                    const int x = 32 * g + k;
-                    fwd[t] |= (uint32_t)((x >> t) & 1) << k;
-                    inv[t] |= (uint32_t)(((x ^ 0x63) >> t) & 1) << k;
-                }
+                for (int k = 0; k < 32; ++k) fwd[t] |= (uint32_t)(((32 * g + k) >> t) & 1) << k;
             }
             sbox_key_lut3(fwd, kp, Lop3Eval{});
-            inv_sbox_key_lut3(inv, kp, Lop3Eval{});
             for (int k = 0; k < 32; ++k) {
-                const int x = 32 * g + k;
-                int f = 0, i = 0;
-                for (int t = 0; t < 8; ++t) {
-                    f |= (int)((fwd[t] >> k) & 1) << t;
-                    i |= (int)((inv[t] >> k) & 1) << t;
-                }
-                if ((f ^ 0x63 ^ key) != kAesTables.sbox[x] || (i ^ key) != kAesTables.inv_sbox[x]) return false;
+                int f = 0;
+                for (int t = 0; t < 8; ++t) f |= (int)((fwd[t] >> k) & 1) << t;
+                if ((f ^ 0x63 ^ key) != kAesTables.sbox[32 * g + k]) return false;
             }
         }
     return true;
 }
-static_assert(check_sbox_lut3(), "the table-mapped S-box networks do not reproduce the S-box");
+static_assert(check_sbox_lut3(), "the table-mapped S-box network does not reproduce the S-box");
 
-// MixColumns and InvMixColumns programs against the column maps written out with
-// GF(2^8) products, on all 32 unit columns at once (plane i holds unit column i in
-// bit i; the maps are linear, so the unit columns decide them).
-constexpr bool check_mix_lut3() {
+// A^-1 on one byte, straight from make_affine_inverse's rows.
+constexpr uint8_t affine_inverse_byte(uint8_t v) {
+    constexpr Rows8 M = make_affine_inverse();
+    uint8_t r = 0;
+    for (int i = 0; i < 8; ++i) {
+        int p = 0;
+        for (int j = 0; j < 8; ++j) p ^= ((M.r[i] >> j) & 1) & ((v >> j) & 1);
+        r |= (uint8_t)(p << i);
+    }
+    return r;
+}
+
+// The linear programs against their maps written out with GF(2^8) products and
+// A^-1, on all unit inputs at once (plane i holds unit vector i in bit i; the
+// maps are linear, so the unit vectors decide them): MixColumns, the decryption
+// column map A^-1 InvMixColumns A^-1 (A^-1 on each byte), and A^-1 on one byte.
+constexpr bool check_linear_lut3() {
     constexpr uint8_t kMix[4] = {2, 3, 1, 1}, kInv[4] = {14, 11, 13, 9};
-    uint32_t m[32] = {}, v[32] = {};
-    for (int i = 0; i < 32; ++i) m[i] = v[i] = 1u << i;
+    uint32_t m[32] = {}, d[32] = {}, f[8] = {};
+    for (int i = 0; i < 32; ++i) m[i] = d[i] = 1u << i;
+    for (int i = 0; i < 8; ++i) f[i] = 1u << i;
     mix_column_lut3(m, Lop3Eval{});
-    inv_mix_column_lut3(v, Lop3Eval{});
+    dec_mix_column_lut3(d, Lop3Eval{});
+    affine_inv_byte_lut3(f, Lop3Eval{});
     for (int i = 0; i < 32; ++i) {
-        uint8_t a[4] = {};
+        uint8_t a[4] = {}, b[4] = {};
         a[i / 8] = (uint8_t)(1u << (i % 8));
+        for (int q = 0; q < 4; ++q) b[q] = affine_inverse_byte(a[q]);
         for (int q = 0; q < 4; ++q) {
-            uint8_t want_m = 0, want_v = 0;
+            uint8_t want_m = 0, inv_mix = 0;
             for (int j = 0; j < 4; ++j) {
                 want_m ^= gf_mul_log(kMix[j], a[(q + j) & 3]);
-                want_v ^= gf_mul_log(kInv[j], a[(q + j) & 3]);
+                inv_mix ^= gf_mul_log(kInv[j], b[(q + j) & 3]);
             }
+            const uint8_t want_d = affine_inverse_byte(inv_mix);
             for (int t = 0; t < 8; ++t) {
                 if (((m[8 * q + t] >> i) & 1u) != ((want_m >> t) & 1u)) return false;
-                if (((v[8 * q + t] >> i) & 1u) != ((want_v >> t) & 1u)) return false;
+                if (((d[8 * q + t] >> i) & 1u) != ((want_d >> t) & 1u)) return false;
             }
         }
     }
+    for (int i = 0; i < 8; ++i) {
+        const uint8_t want = affine_inverse_byte((uint8_t)(1u << i));
+        for (int t = 0; t < 8; ++t)
+            if (((f[t] >> i) & 1u) != ((want >> t) & 1u)) return false;
+    }
     return true;
 }
-static_assert(check_mix_lut3(), "the MixColumns / InvMixColumns programs do not reproduce the column maps");
+static_assert(check_linear_lut3(), "the linear programs do not reproduce their maps");
 
 // Byte permute: byte i of the result is byte (sel >> 4i) & 7 of the eight
 // bytes {a (bytes 0-3), b (bytes 4-7)}; PRMT on the device.
@@ -427,10 +434,17 @@ GBAES_HD inline void mix_half(uint32_t (&s)[64]) {
     mix_column_lut3(&s[32], Lop3{});
 }
 
-// InvMixColumns on the half's two columns, each as a generated XOR program.
-GBAES_HD inline void inv_mix_half(uint32_t (&s)[64]) {
-    inv_mix_column_lut3(&s[0], Lop3{});
-    inv_mix_column_lut3(&s[32], Lop3{});
+// The decryption's column map A^-1 InvMixColumns A^-1 on the half's two columns
+// (see decrypt_half), each as a generated XOR program.
+GBAES_HD inline void dec_mix_half(uint32_t (&s)[64]) {
+    dec_mix_column_lut3(&s[0], Lop3{});
+    dec_mix_column_lut3(&s[32], Lop3{});
+}
+
+// A^-1 on each of the half's 8 bytes.
+GBAES_HD inline void affine_inv_half(uint32_t (&s)[64]) {
+#pragma unroll
+    for (int l = 0; l < 8; ++l) affine_inv_byte_lut3(&s[8 * l], Lop3{});
 }
 
 // SubBytes with the key planes of step r added to its output, on a half.
@@ -462,31 +476,30 @@ GBAES_HD inline void encrypt_half(uint32_t (&s)[64], const Keys& keys, const Oth
     sub_bytes_key_half(s, keys, NR);
 }
 
-// InvSubBytes with the key planes of step r added to its output, on a half.
-template <class Keys>
-GBAES_HD inline void inv_sub_bytes_key_half(uint32_t (&s)[64], const Keys& keys, int r) {
-#pragma unroll
-    for (int l = 0; l < 8; ++l) {
-        uint32_t k[8];
-        keys.load8(r, l, k);
-        inv_sbox_planes_key(&s[8 * l], k);
-    }
-}
-
-// Straight inverse cipher on a half state; keys step r as make_key_planes gives
-// it, added on the inverse S-box output (before InvMixColumns, as the cipher
-// orders it).
+// Straight inverse cipher on a half state, run on t = A^-1 s (A^-1 applied to
+// every byte of the cipher state s).  The inverse S-box is A^-1 F(A^-1 x) for
+// input x already carrying the affine constant (F the S-box without its
+// constant), A^-1 is linear and commutes with InvShiftRows, so a round
+//   s' = InvMixColumns(A^-1 F(A^-1 InvShiftRows(s)) ^ k)
+// becomes, on t,
+//   t' = A^-1 InvMixColumns A^-1 (F(InvShiftRows(t)) ^ A k):
+// the encryption's S-box network with the key planes A k (make_key_planes),
+// then one linear map per column.  The last round has no InvMixColumns: the
+// output is A^-1 (F(InvShiftRows(t)) ^ A k).  The affine constant rides in the
+// key planes as before.
 template <int NR, class Keys, class Other>
 GBAES_HD inline void decrypt_half(uint32_t (&s)[64], const Keys& keys, const Other& other) {
     add_key_half(s, keys, 0);
+    affine_inv_half(s);
 #pragma unroll 1
     for (int r = 1; r < NR; ++r) {
         inv_shift_rows_half(s, other);
-        inv_sub_bytes_key_half(s, keys, r);
-        inv_mix_half(s);
+        sub_bytes_key_half(s, keys, r);
+        dec_mix_half(s);
     }
     inv_shift_rows_half(s, other);
-    inv_sub_bytes_key_half(s, keys, NR);
+    sub_bytes_key_half(s, keys, NR);
+    affine_inv_half(s);
 }
 
 // InvMixColumns of one column word (byte q = row q): out_q = {0e}b_q + {0b}b_{q+1}
@@ -506,13 +519,30 @@ GBAES_HD constexpr uint32_t inv_mix_word(uint32_t w) {
     return (uint32_t)o[0] | (uint32_t)o[1] << 8 | (uint32_t)o[2] << 16 | (uint32_t)o[3] << 24;
 }
 
+// The S-box's affine matrix A (without its constant) on each byte of a word:
+// bit i of a byte becomes b_i ^ b_{i+4} ^ b_{i+5} ^ b_{i+6} ^ b_{i+7}.
+GBAES_HD constexpr uint32_t affine_word(uint32_t w) {
+    uint32_t r = 0;
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t b = (w >> (8 * q)) & 0xffu;
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t bit = ((b >> i) ^ (b >> ((i + 4) & 7)) ^ (b >> ((i + 5) & 7)) ^ (b >> ((i + 6) & 7)) ^
+                                  (b >> ((i + 7) & 7))) & 1u;
+            r |= bit << (8 * q + i);
+        }
+    }
+    return r;
+}
+
 // Key planes (0 or all ones) for each processing step, from a round-key
 // schedule rk (4*(nr+1) words), plane p = 8*(state byte) + bit.
 // Encryption: step 0 is rk[0]; step r (1 <= r < nr) is InvMixColumns(rk[r])
 // XOR 0x63 in every byte, added to the S-box output before MixColumns
 // (MixColumns is linear and maps 0x63 in all four bytes of a column to
-// itself); step nr is rk[nr] XOR 0x63.  Decryption (straight inverse cipher):
-// step r uses rk[nr - r], XORed with 0x63 in every byte for r < nr.
+// itself); step nr is rk[nr] XOR 0x63.  Decryption (straight inverse cipher
+// on A^-1 of the state, see decrypt_half): step 0 is rk[nr] XOR 0x63; step r
+// (r >= 1) is A applied to each byte of rk[nr - r], XORed with 0x63 first for
+// r < nr.
 GBAES_HD inline void make_key_planes(const uint32_t* rk, int nr, bool decrypt, uint32_t (*planes)[128]) {
     for (int r = 0; r <= nr; ++r) {
         const int src = decrypt ? nr - r : r;
@@ -521,6 +551,7 @@ GBAES_HD inline void make_key_planes(const uint32_t* rk, int nr, bool decrypt, u
             uint32_t w = rk[4 * src + p / 32];
             if (!decrypt && r >= 1 && r < nr) w = inv_mix_word(w);
             if (fold) w ^= 0x63636363u;
+            if (decrypt && r >= 1) w = affine_word(w);
             planes[r][p] = ((w >> (p % 32)) & 1u) ? 0xffffffffu : 0u;
         }
     }

@@ -1,5 +1,5 @@
-"""Writes sbox_lut3.h: the bitsliced S-box circuits mapped onto three-input lookup tables,
-and MixColumns / InvMixColumns as programs of two- and three-input XORs.
+"""Writes sbox_lut3.h: the bitsliced S-box circuit mapped onto three-input lookup tables,
+and the linear maps the rounds need as programs of two- and three-input XORs.
 
 The bitsliced kernel spends most of its integer-ALU instructions in the S-box
 circuit (bitsliced.h, `sbox_circuit`: Boyar and Peralta's depth-16 circuit, 34
@@ -9,14 +9,16 @@ cover of its gates by three-input cones.  This script
 
   1. reads the gate list of `sbox_circuit` from bitsliced.h (one source for the
      circuit; its exhaustive compile-time check stays where it is),
-  2. builds the two networks the kernel evaluates per state byte: the S-box with
-     a round-key plane XORed onto each output bit (encryption), and the inverse
-     S-box A^-1 F(A^-1 x) with the same key XOR (decryption; A^-1 the inverse of
-     the S-box's affine matrix, F the circuit),
+  2. builds the network the kernel evaluates per state byte: the S-box without
+     its affine constant, F, with a round-key plane XORed onto each output bit.
+     Decryption runs the same network: it works on A^-1 of the state (A the
+     S-box's affine matrix), where the inverse S-box A^-1 F(A^-1 x) leaves F
+     alone and the two A^-1 move into the linear map around it (bitsliced.h,
+     decrypt_half),
   3. re-brackets the XOR sums the circuit computes once (maximal trees of XOR
      gates whose inner results feed nothing else: any bracketing of the same
      terms gives the same sum), each tree as recorded in SHAPES below,
-  4. maps each network onto three-input lookup tables: every 3-feasible cut of
+  4. maps the network onto three-input lookup tables: every 3-feasible cut of
      every gate is enumerated, each gate takes the cut of least area flow, and
      passes of exact-area recovery then re-choose cuts where that frees the most
      tables (the standard cut-based technology-mapping method of FPGA tools),
@@ -24,26 +26,27 @@ cover of its gates by three-input cones.  This script
      PTX's lop3 encoding (bit i = F(i >> 2 & 1, i >> 1 & 1, i & 1) for operands
      a, b, c), in the order the network computes them.
 
-The column maps (the 32x32 GF(2) matrices of MixColumns and InvMixColumns over
-a column's 32 bit planes) are written as straight-line programs by a greedy
-method in the manner of Paar's (1997) common-subexpression algorithm, adapted
-to three-input gates: while some output still needs more than one gate, create
-the XOR of the pair or triple of available signals whose creation lowers the
-remaining three-input-gate count most, ties broken by a seeded jitter; each
-output then sums its remaining signals three at a time.  MIX_SEEDS records the
-jitter seed with the fewest gates among 64 (`--search-mix`): MixColumns 56
-tables per column, InvMixColumns 101 (the kernel's xtime forms took 76 and 118).
+The linear maps -- MixColumns on a column's 32 bit planes, the decryption's
+column map A^-1 InvMixColumns A^-1 (A^-1 on each byte), and A^-1 on one byte --
+are written as straight-line programs by a greedy method in the manner of
+Paar's (1997) common-subexpression algorithm, adapted to three-input gates:
+while some output still needs more than one gate, create the XOR of the pair or
+triple of available signals whose creation lowers the remaining three-input-gate
+count most, ties broken by a seeded jitter; each output then sums its remaining
+signals three at a time.  MIX_SEEDS records the jitter seed with the fewest
+gates among 64 (`--search-mix`).  MixColumns takes 56 tables per column where
+its xtime form took 76; the decryption's column map 122, and with it each
+inverse S-box is the 81-table forward network instead of a 102-table one.
 
 The bracketings in SHAPES come from `--search`: a hill climb that re-draws one
 tree's bracketing at a time and keeps the draw when the mapped table count does
-not grow (encryption 91 -> 81 tables, decryption 110 -> 102 from the circuit's
-own bracketing).  A tree's entry seeds the splitmix64 generator that picks
-which two of its remaining terms to XOR next; trees without an entry keep the
-circuit's bracketing.
+not grow (91 -> 81 tables from the circuit's own bracketing).  A tree's entry
+seeds the splitmix64 generator that picks which two of its remaining terms to
+XOR next; trees without an entry keep the circuit's bracketing.
 
 Run from anywhere: python gen_sbox_lut3.py [--out PATH]  (default: rewrites sbox_lut3.h next to it);
-python gen_sbox_lut3.py --search enc|dec [--iters N] [--seed S] prints a new SHAPES entry;
-python gen_sbox_lut3.py --search-mix mix|inv_mix [--seed S] prints the best of 64 seeds from S.
+python gen_sbox_lut3.py --search [--iters N] [--seed S] prints a new SHAPES entry;
+python gen_sbox_lut3.py --search-mix mix|dec_mix|affine_inv [--seed S] prints the best of 64 seeds from S.
 """
 import argparse
 import itertools
@@ -119,19 +122,6 @@ def encrypt_net():
     o = net.add_circuit("c_", [f"x{7 - i}" for i in range(8)])
     for t in range(8):
         net.outs.append(net.gate(f"y{t}", "^", o[7 - t], f"k{t}"))
-    return net
-
-
-def decrypt_net():
-    """x[t] (input already XORed with the affine constant) -> A^-1 F(A^-1 x)[t] ^ k[t]."""
-    rows = affine_inverse_rows()
-    net = Net([f"x{t}" for t in range(8)] + [f"k{t}" for t in range(8)])
-    z = [net.xor_chain(f"z{i}", [f"x{j}" for j in range(8) if (rows[i] >> j) & 1]) for i in range(8)]
-    o = net.add_circuit("c_", [z[7 - i] for i in range(8)])
-    f = [o[7 - t] for t in range(8)]
-    for i in range(8):
-        terms = [f[j] for j in range(8) if (rows[i] >> j) & 1] + [f"k{i}"]
-        net.outs.append(net.xor_chain(f"y{i}", terms))
     return net
 
 
@@ -376,13 +366,13 @@ def column_rows(coef):
     return rows
 
 
-def xor_program(rows, seed):
+def xor_program(rows, seed, n_in=32):
     """A straight-line program of XORs of two or three signals computing every row (greedy: repeatedly
     create the sum of the pair or triple of signals that lowers the three-input-gate cost of the
     remaining rows most, a seeded jitter breaking ties).  Returns (steps, rows as signal sets); step k
-    creates signal 32 + k as the XOR of its operands."""
+    creates signal n_in + k as the XOR of its operands."""
     rng = SplitMix64(seed)
-    rows_s = [set(i for i in range(32) if (r >> i) & 1) for r in rows]
+    rows_s = [set(i for i in range(n_in) if (r >> i) & 1) for r in rows]
 
     def cost(k):
         return k // 2 if k > 1 else 0  # three-input gates to sum k signals: ceil((k - 1) / 2)
@@ -404,7 +394,7 @@ def xor_program(rows, seed):
                 best, best_v = c, v
         if best is None:
             break
-        new = 32 + len(steps)
+        new = n_in + len(steps)
         steps.append(best)
         for rs in rows_s:
             if len(rs) > 1 and all(x in rs for x in best):
@@ -413,11 +403,10 @@ def xor_program(rows, seed):
     return steps, rows_s
 
 
-def emit_linear(fname, what, steps, rows_s):
-    """The program as lop calls on 32 planes in place (x[8q + t] = bit t of byte q of the column)."""
-    names = {i: f"x[{i}]" for i in range(32)}
-    lines = [f"    const uint32_t i{i} = x[{i}];" for i in range(32)]
-    names = {i: f"i{i}" for i in range(32)}
+def emit_linear(fname, what, steps, rows_s, n_in=32):
+    """The program as lop calls on n_in planes in place."""
+    lines = [f"    const uint32_t i{i} = x[{i}];" for i in range(n_in)]
+    names = {i: f"i{i}" for i in range(n_in)}
     xor2, xor3 = 0x3C, 0x96  # a ^ b (third operand repeats a), a ^ b ^ c
     n = 0
 
@@ -432,7 +421,7 @@ def emit_linear(fname, what, steps, rows_s):
         return v
 
     for k, ops in enumerate(steps):
-        names[32 + k] = lop([names[o] for o in ops])
+        names[n_in + k] = lop([names[o] for o in ops])
     outs = []
     for rs in rows_s:
         terms = [names[o] for o in sorted(rs)]
@@ -446,13 +435,43 @@ def emit_linear(fname, what, steps, rows_s):
     return head + "\n" + "\n".join(lines) + "\n}\n", n
 
 
-# The column maps: MixColumns (02 03 01 01) and InvMixColumns (0e 0b 0d 09), as coefficient rows.
-MIX_COEF = {"mix": (2, 3, 1, 1), "inv_mix": (14, 11, 13, 9)}
+def affine_inverse_byte(v):
+    """A^-1 applied to one byte (bit i of the result = parity of row i of A^-1 and v)."""
+    rows = affine_inverse_rows()
+    return sum((bin(rows[i] & v).count("1") & 1) << i for i in range(8))
+
+
+def matrix_rows(f, n):
+    """Rows (bit masks over the n input bits) of the GF(2)-linear map f on n-bit vectors."""
+    cols = [f(1 << j) for j in range(n)]
+    return [sum(((cols[j] >> r) & 1) << j for j in range(n)) for r in range(n)]
+
+
+def bytewise(f):
+    return lambda v: sum(f((v >> (8 * q)) & 0xFF) << (8 * q) for q in range(4))
+
+
+def linear_maps():
+    """name -> (rows, inputs): MixColumns of a column; the decryption column map A^-1 InvMixColumns A^-1
+    (bytewise A^-1 on both sides, see bitsliced.h); A^-1 on one byte."""
+    inv_rows = column_rows((14, 11, 13, 9))
+
+    def apply(rows, v):
+        return sum((bin(row & v).count("1") & 1) << r for r, row in enumerate(rows))
+
+    ainv = bytewise(affine_inverse_byte)
+    return {
+        "mix": (column_rows((2, 3, 1, 1)), 32),
+        "dec_mix": (matrix_rows(lambda v: ainv(apply(inv_rows, ainv(v))), 32), 32),
+        "affine_inv": (matrix_rows(affine_inverse_byte, 8), 8),
+    }
+
+
 # Seeds of the greedy XOR programs, chosen by --search-mix (the program with the fewest gates of 64 seeds).
-MIX_SEEDS = {"mix": 8, "inv_mix": 57}
+MIX_SEEDS = {"mix": 8, "dec_mix": 54, "affine_inv": 0}
 
 
-# Bracketings found by --search (seed 1, 1,500 steps each): tree root -> splitmix64 seed.
+# Bracketings found by --search (seed 1, 1,500 steps): tree root -> splitmix64 seed.
 SHAPES = {
     "enc": {
         "c_l6": 8411996437093593279,
@@ -473,87 +492,56 @@ SHAPES = {
         "y6": 65468312225334051,
         "y7": 5208041666417506291,
     },
-    "dec": {
-        "c_l6": 15053352997926904907,
-        "c_m20": 17208915671098355703,
-        "c_m21": 7467859444893362743,
-        "c_m22": 10174854292179124725,
-        "c_m23": 13900687464464979805,
-        "c_m38": 2243067523905852675,
-        "c_m40": 6572600082127798947,
-        "c_s0": 7589964776984157073,
-        "c_s1": 12327957813683028421,
-        "c_s2": 14618154987885078747,
-        "c_s3": 2037386553481293547,
-        "c_s4": 13290268570847108467,
-        "c_s5": 17508866225838119887,
-        "c_s6": 13993476446138047205,
-        "c_s7": 15305350299310617173,
-        "c_t19": 5208041666417506291,
-        "c_t22": 12677037431724280505,
-        "c_t5": 3078487764655139347,
-        "y0_2": 3836897347045491961,
-        "y1_2": 17537885973340814571,
-        "y2_2": 15563214200757333989,
-        "y3_2": 961137476199508239,
-        "y4_2": 1536169924725109803,
-        "y5_2": 7880484762772585691,
-        "y6_2": 7710113369677980097,
-        "y7_2": 1501121449731526029,
-        "z0_1": 12944380480760822807,
-        "z1_1": 15459438588758570425,
-        "z2_1": 12110998379208263153,
-        "z4_1": 14080516419620970537,
-        "z5_1": 6682256367785181475,
-        "z6_1": 15587678707349028255,
-        "z7_1": 17978135531838172359,
-    },
 }
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=os.path.join(HERE, "sbox_lut3.h"))
-    ap.add_argument("--search", choices=("enc", "dec"))
-    ap.add_argument("--search-mix", choices=tuple(MIX_COEF))
+    ap.add_argument("--search", action="store_true", help="hill-climb the S-box network's bracketings")
+    ap.add_argument("--search-mix", choices=tuple(MIX_SEEDS))
     ap.add_argument("--iters", type=int, default=1500)
     ap.add_argument("--seed", type=int, default=1)
     args = ap.parse_args()
+    maps = linear_maps()
     if args.search_mix:
-        rows = column_rows(MIX_COEF[args.search_mix])
+        rows, n_in = maps[args.search_mix]
         counts = []
         for sd in range(args.seed, args.seed + 64):
-            steps, rows_s = xor_program(rows, sd)
+            steps, rows_s = xor_program(rows, sd, n_in)
             counts.append((len(steps) + sum(len(r) // 2 for r in rows_s if len(r) > 1), sd))
         print("fewest gates, seed:", min(counts))
         return
     if args.search:
-        net = encrypt_net() if args.search == "enc" else decrypt_net()
+        net = encrypt_net()
         shapes = search(net, args.iters, args.seed)
         print(len(map_lut3(reshape(net, shapes))), "tables;", dict(sorted(shapes.items())))
         return
     out = args.out
-    enc, dec = reshape(encrypt_net(), SHAPES["enc"]), reshape(decrypt_net(), SHAPES["dec"])
-    enc_cover, dec_cover = map_lut3(enc), map_lut3(dec)
-    mix_code, mix_n = emit_linear(
-        "mix_column_lut3", "MixColumns of one column in place: out_q = 02 a_q + 03 a_q+1 + a_q+2 + a_q+3.",
-        *xor_program(column_rows(MIX_COEF["mix"]), MIX_SEEDS["mix"]))
-    inv_code, inv_n = emit_linear(
-        "inv_mix_column_lut3", "InvMixColumns of one column in place: out_q = 0e a_q + 0b a_q+1 + 0d a_q+2 + 09 a_q+3.",
-        *xor_program(column_rows(MIX_COEF["inv_mix"]), MIX_SEEDS["inv_mix"]))
+    enc = reshape(encrypt_net(), SHAPES["enc"])
+    enc_cover = map_lut3(enc)
+    code, count = {}, {}
+    what = {
+        "mix": ("mix_column_lut3", "MixColumns of one column in place: out_q = 02 a_q + 03 a_q+1 + a_q+2 + a_q+3."),
+        "dec_mix": ("dec_mix_column_lut3", "Decryption's column map in place: A^-1 InvMixColumns A^-1 (A^-1 bytewise)."),
+        "affine_inv": ("affine_inv_byte_lut3", "A^-1 (the inverse of the S-box's affine matrix) on one byte in place."),
+    }
+    for name, (rows, n_in) in maps.items():
+        code[name], count[name] = emit_linear(what[name][0], what[name][1],
+                                              *xor_program(rows, MIX_SEEDS[name], n_in), n_in=n_in)
     text = f"""// Generated by gen_sbox_lut3.py from sbox_circuit in bitsliced.h -- do not edit.
 //
-// The bitsliced S-box networks as three-input lookup tables (one LOP3 each on
-// the GPU): sbox_key_lut3 computes x[t] = S(x)[t] ^ k[t] without the affine
-// constant ({len(enc_cover)} tables for the {len(enc.gates)} two-input gates of the circuit plus the key
-// XORs); inv_sbox_key_lut3 computes x[t] = A^-1 F(A^-1 x)[t] ^ k[t] for input
-// already XORed with the affine constant ({len(dec_cover)} tables for {len(dec.gates)} gates).  Planes are
-// indexed by bit (x[0] = least significant).  mix_column_lut3 and
-// inv_mix_column_lut3 compute MixColumns ({mix_n} tables) and InvMixColumns ({inv_n}) on
-// the 32 planes of one state column (x[8q + t] = bit t of row q) as greedy
-// programs of two- and three-input XORs.  lop(a, b, c, Tt<imm>) returns the
-// function whose truth table imm lists F(a, b, c) at bit 4a + 2b + c (the table
-// travels as a type, so that it stays a compile-time constant).
+// The bitsliced S-box network as three-input lookup tables (one LOP3 each on
+// the GPU): sbox_key_lut3 computes x[t] = F(x)[t] ^ k[t], F the S-box without its
+// affine constant ({len(enc_cover)} tables for the {len(enc.gates)} two-input gates of the circuit plus
+// the key XORs).  Planes are indexed by bit (x[0] = least significant).  The
+// linear maps as greedy programs of two- and three-input XORs: mix_column_lut3
+// is MixColumns ({count["mix"]} tables) and dec_mix_column_lut3 the decryption's
+// A^-1 InvMixColumns A^-1 ({count["dec_mix"]}), on the 32 planes of one state column
+// (x[8q + t] = bit t of row q); affine_inv_byte_lut3 is A^-1 on one byte's 8
+// planes ({count["affine_inv"]}).  lop(a, b, c, Tt<imm>) returns the function whose truth
+// table imm lists F(a, b, c) at bit 4a + 2b + c (the table travels as a type, so
+// that it stays a compile-time constant).
 #pragma once
 
 #include <cstdint>
@@ -574,15 +562,16 @@ template <uint32_t V>
 using Tt = std::integral_constant<uint32_t, V>;
 
 {emit(enc, enc_cover, "sbox_key_lut3")}
-{emit(dec, dec_cover, "inv_sbox_key_lut3")}
-{mix_code}
-{inv_code}
+{code["mix"]}
+{code["dec_mix"]}
+{code["affine_inv"]}
 }}  // namespace bs
 }}  // namespace gbaes
 """
     with open(out, "w") as f:
         f.write(text)
-    print(f"{os.path.basename(out)}: {len(enc_cover)} + {len(dec_cover)} tables, mix {mix_n} + {inv_n}")
+    print(f"{os.path.basename(out)}: S-box {len(enc_cover)} tables; "
+          + ", ".join(f"{k} {v}" for k, v in count.items()))
 
 
 if __name__ == "__main__":
