@@ -748,7 +748,9 @@ class OpenSSLECB:
 def run_cpu_sweep():
     """CPU comparison at the paper's Fig. 4 granularity (1, 2, 3, 4 cores and all
     cores): the oracle and, when present, OpenSSL's EVP AES-ECB; AES-128/256
-    encryption of large buffers; reporting only."""
+    encryption of large buffers; then the oracle beside the bench's six
+    operations: one core on a 64 MiB slice and all cores on the whole 1 GiB
+    buffer, AES-128/192/256 encryption and decryption.  Reporting only."""
     import numpy as np
     from concurrent.futures import ThreadPoolExecutor
 
@@ -787,6 +789,17 @@ def run_cpu_sweep():
             print(json.dumps({"sweep": "cpu", "impl": "openssl-evp", "version": ossl.version, "bits": bits,
                               "threads": n, "bytes": data.size, "gbs": data.size / best / 1e9,
                               "matches_oracle": bool(ok)}), flush=True)
+    for bits in BITS:
+        key = workloads.random_key(workloads.SEED_BULK[bits], bits)
+        for n, size in ((1, 64 * MiB), (allc, GiB)):
+            data = workloads.host_bytes(workloads.SEED_BULK[bits], size)
+            for dec in (False, True):
+                t0 = time.perf_counter()
+                oracle.ecb(key, bits, data, decrypt=dec, nthreads=n)
+                dt = time.perf_counter() - t0
+                print(json.dumps({"sweep": "cpu-oracle-bench-ops", "impl": "oracle", "bits": bits,
+                                  "op": "dec" if dec else "enc", "threads": n, "bytes": data.size,
+                                  "gbs": data.size / dt / 1e9}), flush=True)
 
 
 def run_serve_sweep(args):
