@@ -17,14 +17,18 @@
 //  * The inverse S-box reuses the same circuit: with F(z) = A inv(z) (the
 //    circuit without the constant, A the affine matrix), the inverse S-box of
 //    y is inv(A^-1 (y ^ 0x63)) = A^-1 F(A^-1 (y ^ 0x63)), the XOR with 0x63
-//    again folded into the round keys; A^-1 costs one three-input XOR per bit.
+//    again folded into the round keys.  Decryption runs on A^-1 of the state,
+//    where the two A^-1 join InvMixColumns and each inverse S-box is F itself
+//    (decrypt_half).
 //  * ShiftRows is a renaming of planes (across the two halves of a split state,
-//    see "half states" below); MixColumns, InvMixColumns and AddRoundKey are
-//    XORs (the column maps as generated XOR programs, sbox_lut3.h).
+//    see "half states" below); MixColumns, the decryption's column map and
+//    AddRoundKey are XORs.
 //
-// The circuit is checked exhaustively at compile time against the S-box of
-// aes_tables.h (static_asserts below).  Everything here is plain C++ usable on
-// the host as well as on the device.
+// The kernel runs F as a cover by three-input lookup tables and the column
+// maps as generated XOR programs (sbox_lut3.h, one LOP3 each).  The circuit and
+// those programs are checked at compile time against the S-box and the column
+// maps of aes_tables.h (static_asserts below).  Everything here is plain C++
+// usable on the host as well as on the device.
 #pragma once
 
 #include <cstdint>

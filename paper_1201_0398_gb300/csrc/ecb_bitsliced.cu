@@ -7,7 +7,8 @@
 // with a coalesced 8-byte load (the warp reads 256 contiguous bytes per load),
 // transposes its two 32x32 bit matrices in registers, runs the rounds as
 // bitwise logic with no memory lookups (ShiftRows trades four bytes' planes
-// with the other lane of the pair by shuffle), transposes back and stores.
+// with the other lane of the pair by shuffle; the S-box and the column maps as
+// generated LOP3 programs), transposes back and stores.
 // Splitting the state halves the registers a lane needs (four CTAs of 128
 // threads per SM instead of two) and the unrolled round body each lane runs.
 // Round-key planes (0 or all ones, the S-box's affine constant folded in) are
