@@ -103,7 +103,7 @@ int aes_decrypt_ecb(const aes_ctx* ctx, const void* in, void* out, size_t nblock
 /* ECB with an explicit kernel choice, for benchmarking and tuning.
  * decrypt: 0/1.  kernel: AES_KERNEL_*.  threads: CTA size, a multiple of 32 in
  * [64, 1024] (0 = default; checked, but the bitsliced kernel always runs
- * 128-thread CTAs, its shape fixed by its 128 registers per thread).
+ * 128-thread CTAs, its shape fixed by its register budget).
  * blocks_per_thread: 1, 2 or 4 for the table kernel (0 = default; the
  * bitsliced kernel always holds 32 blocks per pair of lanes). */
 int aes_ecb_ex(const aes_ctx* ctx, int decrypt, const void* in, void* out, size_t nblocks, int kernel,

@@ -10,7 +10,8 @@
 // with the other lane of the pair by shuffle; the S-box and the column maps as
 // generated LOP3 programs), transposes back and stores.
 // Splitting the state halves the registers a lane needs (four CTAs of 128
-// threads per SM instead of two) and the unrolled round body each lane runs.
+// threads per SM instead of two; five for encryption, whose column map is
+// smaller and fits 96 registers) and the unrolled round body each lane runs.
 // Round-key planes (0 or all ones, the S-box's affine constant folded in) are
 // staged once per CTA in shared memory, each half's row in its own banks.  The
 // kernel is bound by the integer pipe, not by shared memory: it is the measured
@@ -23,7 +24,8 @@
 namespace gbaes {
 
 constexpr int kBsThreads = 128;
-constexpr int kBsCtasPerSm = 4;
+constexpr int kBsCtasPerSmEnc = 5;  // 96 registers per thread (20 warps per SM)
+constexpr int kBsCtasPerSmDec = 4;  // 128 registers per thread
 constexpr int kBsWarpBlocks = 512;  // 16 lane pairs x 32 blocks
 
 struct BsArgs {
@@ -39,7 +41,8 @@ struct PairShuffle {
 };
 
 template <int NR, bool DEC>
-__global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitsliced_kernel(const __grid_constant__ BsArgs a) {
+__global__ void __launch_bounds__(kBsThreads, DEC ? kBsCtasPerSmDec : kBsCtasPerSmEnc)
+    bitsliced_kernel(const __grid_constant__ BsArgs a) {
     __shared__ __align__(16) uint32_t keys_s[(NR + 1) * bs::kKeyStepWords];
     for (int i = threadIdx.x; i < (NR + 1) * bs::kKeyStepWords; i += blockDim.x) keys_s[i] = a.planes[i];
     __syncthreads();
@@ -97,7 +100,7 @@ int launch_bitsliced(const EcbArgs& e, const uint32_t* enc_rk, int nr, Mode mode
     const bool dec = mode == kDec;
     BsKernel fn = pick_bs(nr, dec);
     if (!fn) return fail(AES_ERR_ARG, "no bitsliced kernel for nr=%d", nr);
-    (void)threads;  // the kernel's shape is fixed by its register budget: 128 threads, 4 CTAs per SM
+    (void)threads;  // the kernel's shape is fixed by its register budget: 128 threads, 4-5 CTAs per SM
     static BsArgs a;  // 8.2 KB: built here, copied into the launch by value
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);

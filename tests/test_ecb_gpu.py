@@ -265,11 +265,12 @@ def test_bitsliced_kernel_vs_oracle(gbaes, bits):
     """The Boolean-circuit kernel (a lane pair holds 32 blocks as bit planes, split
     by state columns; a warp takes 512 blocks, a CTA 2,048): edge sizes around a
     pair's, a warp's and a CTA's tile, and more than one pass of the full grid
-    (152 SMs x 4 CTAs x 2,048 blocks) with a ragged tail."""
+    (152 SMs x 4 CTAs for decryption, x 5 for encryption, x 2,048 blocks) with a
+    ragged tail."""
     rng = np.random.default_rng(900 + bits)
     key = rng.integers(0, 256, bits // 8, dtype=np.uint8).tobytes()
     k = gbaes.Key(key)
-    for n in (1, 15, 16, 17, 31, 33, 511, 512, 513, 2047, 2049, 4097, sms() * 4 * 2048 + 2048 * 3 + 5):
+    for n in (1, 15, 16, 17, 31, 33, 511, 512, 513, 2047, 2049, 4097, sms() * 5 * 2048 + 2048 * 3 + 5):
         data = rng.integers(0, 256, 16 * n, dtype=np.uint8)
         for decrypt in (False, True):
             out = gbaes.ecb_ex(k, dev(data), decrypt=decrypt, kernel=gbaes.KERNEL_BITSLICED)
