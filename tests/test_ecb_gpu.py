@@ -19,7 +19,8 @@ BITS = (128, 192, 256)
 
 
 def dev(a: np.ndarray):
-    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    a = np.ascontiguousarray(a)
+    return torch.from_numpy(a if a.flags.writeable else a.copy()).cuda()
 
 
 def host(t) -> np.ndarray:
