@@ -371,6 +371,8 @@ typedef struct aes_server_diag {
     uint64_t producer_check_at_ns;
     int64_t sched_cpu;                  /* CPU the scheduler thread is pinned to (AES_SERVER_PIN_THREADS), else -1 */
     int64_t producer_cpu;               /* CPU the replay thread is pinned to, else -1 */
+    uint64_t sched_minflt;              /* minor page faults of the scheduler thread (sampled with its windows) */
+    uint64_t producer_minflt;           /* replay: minor page faults over all replays */
 } aes_server_diag;
 
 /* Copies the server's host-thread diagnostics. */
@@ -401,7 +403,8 @@ int aes_server_replay_join(aes_server* server, int stop_early);
  * AES_ERR_STATE on timeout. */
 int aes_server_drain(aes_server* server, double timeout_s);
 
-/* Moves up to max completions into out; returns how many. */
+/* Moves up to max completions (at most 2^31-1 per call) into out, oldest first;
+ * returns how many. */
 int aes_server_poll(aes_server* server, aes_server_completion* out, size_t max);
 
 /* Copies the server's counters. */

@@ -488,7 +488,8 @@ class _ServerDiag(ctypes.Structure):
                  ("inbox_hold_max_ns", ctypes.c_uint64 * 2)] +
                 [(n, ctypes.c_uint64) for n in ("producer_late_max_ns", "producer_late_at_ns", "producer_late_invol",
                                                 "producer_invol", "producer_check_max_ns", "producer_check_at_ns")] +
-                [("sched_cpu", ctypes.c_int64), ("producer_cpu", ctypes.c_int64)])
+                [("sched_cpu", ctypes.c_int64), ("producer_cpu", ctypes.c_int64),
+                 ("sched_minflt", ctypes.c_uint64), ("producer_minflt", ctypes.c_uint64)])
 
 
 class Server:

@@ -58,6 +58,141 @@ struct Pending {
     double arrival;  // seconds on the server clock
 };
 
+// Completions waiting for aes_server_poll: a FIFO of fixed-size chunks.
+// Chunks are made ahead of use (reserve: page-locked when a GPU is present, so
+// the kernel's memory compaction cannot move them, and every page touched when
+// made), and a chunk emptied by poll is kept for reuse.  Appending on the
+// scheduler thread therefore normally calls no allocator and touches no page
+// it has not touched before: a page fault there (a fresh page, or a page being
+// migrated) can block for tens of milliseconds, and every thread waiting on the
+// completion lock with it.  It grows without copying what it holds and
+// releases from the front.
+class CompletionFifo {
+  public:
+    static constexpr size_t kChunk = 16384;  // completions per chunk (640 KiB)
+
+    CompletionFifo() = default;
+    CompletionFifo(const CompletionFifo&) = delete;
+    CompletionFifo& operator=(const CompletionFifo&) = delete;
+    ~CompletionFifo() {
+        for (Chunk* c : live_) drop(c);
+        for (Chunk* c : spare_) drop(c);
+    }
+
+    void set_page_locked(bool v) { page_locked_ = v; }
+    size_t size() const { return size_; }
+
+    // Room for n more completions than are held now, made ahead of use.
+    // Returns false when memory runs out (the FIFO still works: push then
+    // allocates as it goes).
+    bool reserve(size_t n) {
+        const size_t free_in_tail = live_.empty() ? 0 : kChunk - tail_;
+        size_t room = free_in_tail + kChunk * spare_.size();
+        while (room < n) {
+            Chunk* c = make(page_locked_);
+            if (!c) return false;
+            spare_.push_back(c);
+            room += kChunk;
+        }
+        const size_t chunks = live_.size() + spare_.size();
+        if (live_.capacity() < chunks) live_.reserve(chunks);
+        if (spare_.capacity() < chunks) spare_.reserve(chunks);
+        return true;
+    }
+
+    // Appends n completions.  Returns false (appending what fits) only when a
+    // chunk cannot be allocated.
+    bool push(const aes_server_completion* c, size_t n) {
+        while (n) {
+            if (live_.empty() || tail_ == kChunk) {
+                Chunk* k = nullptr;
+                if (!spare_.empty()) {
+                    k = spare_.back();
+                    spare_.pop_back();
+                } else {
+                    k = make(false);  // (no spare left: a plain allocation, touched as it fills)
+                    if (!k) return false;
+                }
+                live_.push_back(k);
+                tail_ = 0;
+            }
+            const size_t m = std::min(n, kChunk - tail_);
+            memcpy(live_.back()->e + tail_, c, m * sizeof(*c));
+            tail_ += m;
+            size_ += m;
+            c += m;
+            n -= m;
+        }
+        return true;
+    }
+
+    // Moves up to max of the oldest completions to out; returns how many.
+    size_t pop(aes_server_completion* out, size_t max) {
+        size_t got = 0;
+        while (got < max && size_) {
+            const size_t end = live_.size() == 1 ? tail_ : kChunk;
+            const size_t m = std::min(max - got, end - head_);
+            memcpy(out + got, live_.front()->e + head_, m * sizeof(*out));
+            head_ += m;
+            got += m;
+            size_ -= m;
+            if (head_ == end) {
+                if (live_.size() == 1) {  // empty: the chunk stays, refilled from its start
+                    head_ = tail_ = 0;
+                } else {
+                    spare_.push_back(live_.front());
+                    live_.erase(live_.begin());
+                    head_ = 0;
+                }
+            }
+        }
+        return got;
+    }
+
+  private:
+    struct Chunk {
+        bool page_locked;
+        aes_server_completion e[kChunk];
+    };
+
+    static Chunk* make(bool page_locked) {
+        void* p = nullptr;
+        if (page_locked) {
+            if (cudaHostAlloc(&p, sizeof(Chunk), cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                p = nullptr;
+                page_locked = false;
+            }
+        }
+        if (!p) {
+            p = malloc(sizeof(Chunk));
+            if (!p) return nullptr;
+        }
+        memset(p, 0, sizeof(Chunk));  // every page touched now, not when a completion lands on it
+        Chunk* c = static_cast<Chunk*>(p);
+        c->page_locked = page_locked;
+        return c;
+    }
+
+    static void drop(Chunk* c) {
+        if (c->page_locked)
+            cudaFreeHost(c);
+        else
+            free(c);
+    }
+
+    std::vector<Chunk*> live_;   // oldest first; the last one is being filled
+    std::vector<Chunk*> spare_;  // made ahead, or emptied by pop
+    size_t head_ = 0;            // next to pop, in live_.front()
+    size_t tail_ = 0;            // next free entry in live_.back()
+    size_t size_ = 0;
+    bool page_locked_ = false;
+};
+
+// Completions made up front when a server starts, and kept spare beyond a
+// replay's own requests when it starts.
+constexpr size_t kCompletionsAhead = 4 * CompletionFifo::kChunk;
+
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -96,7 +231,7 @@ struct ThreadWatch {
     uint32_t passes = 0;
     uint64_t npasses = 0;
     double worst_wall = 0, worst_cpu = 0, worst_at = 0;
-    long worst_invol = 0, worst_vol = 0, worst_minflt = 0, worst_majflt = 0, invol_total = 0;
+    long worst_invol = 0, worst_vol = 0, worst_minflt = 0, worst_majflt = 0, invol_total = 0, minflt_total = 0;
 
     static void usage(double* cpu, long* invol, long* vol = nullptr, long* minflt = nullptr, long* majflt = nullptr) {
         struct rusage u;
@@ -115,6 +250,7 @@ struct ThreadWatch {
         usage(&cpu, &invol, &vol, &minflt, &majflt);
         if (started) {
             invol_total += invol - invol_start;
+            minflt_total += minflt - minflt_start;
             if (win_busy && now - win_start > worst_wall) {
                 worst_wall = now - win_start;
                 worst_cpu = cpu - cpu_start;
@@ -173,10 +309,7 @@ struct aes_server {
     uint64_t batch_counter = 0;   // scheduler thread only
 
     std::mutex out_mu;
-    // Completions waiting for aes_server_poll.  A deque: it grows without copying what it holds (a vector's
-    // reallocation copied hundreds of MB under out_mu and stalled the scheduler for tens of ms) and
-    // releases from the front.
-    std::deque<aes_server_completion> done;
+    CompletionFifo done;  // completions waiting for aes_server_poll (under out_mu)
 
     std::mutex stats_mu;
     aes_server_stats stats{};
@@ -326,6 +459,7 @@ static void publish_diagnostics(aes_server* S) {
     d.sched_worst_window_minflt = (uint64_t)w.worst_minflt;
     d.sched_worst_window_majflt = (uint64_t)w.worst_majflt;
     d.sched_invol = (uint64_t)w.invol_total;
+    d.sched_minflt = (uint64_t)w.minflt_total;
     for (int i = 0; i < 3; ++i) {
         d.lock_wait_max_ns[i] = (uint64_t)(1e9 * S->lock_wait_max[i]);
         d.lock_wait_at_ns[i] = (uint64_t)(1e9 * S->lock_wait_at[i]);
@@ -344,21 +478,18 @@ static void publish_diagnostics(aes_server* S) {
 }
 
 static void complete(aes_server* S, std::vector<Pending>& reqs, int status, double launch_s, double done_s) {
-    std::vector<aes_server_completion> out;
-    out.reserve(reqs.size());
-    for (const Pending& p : reqs) {
-        aes_server_completion c;
-        c.id = p.r.id;
-        c.status = status;
-        c.batch_msgs = (uint32_t)reqs.size();
-        c.arrival_s = p.arrival;
-        c.launch_s = launch_s;
-        c.done_s = done_s;
-        out.push_back(c);
-    }
     {
         SchedLock lk(S, kLockDone);
-        S->done.insert(S->done.end(), out.begin(), out.end());
+        for (const Pending& p : reqs) {
+            aes_server_completion c;
+            c.id = p.r.id;
+            c.status = status;
+            c.batch_msgs = (uint32_t)reqs.size();
+            c.arrival_s = p.arrival;
+            c.launch_s = launch_s;
+            c.done_s = done_s;
+            S->done.push(&c, 1);
+        }
     }
     {
         SchedLock lk(S, kLockStats);
@@ -476,6 +607,7 @@ static bool idle_wait(aes_server* S, bool idle) {
 
 static void scheduler_main(aes_server* S) {
     if (!S->dryrun) cudaSetDevice(S->device);
+    pthread_setname_np(pthread_self(), "gbaes-sched");  // (names for ps, top and /proc/<pid>/task)
     if (S->cfg.flags & AES_SERVER_PIN_THREADS) S->sched_cpu = pin_thread(0);
     for (;;) {
         S->sched_watch.pass(S->now(), !S->sched_slept);
@@ -809,6 +941,7 @@ static bool publish(aes_server* S, const Pending& p, uint64_t bytes, double now)
 
 static void scheduler_resident(aes_server* S) {
     if (!S->dryrun) cudaSetDevice(S->device);
+    pthread_setname_np(pthread_self(), "gbaes-sched");  // (names for ps, top and /proc/<pid>/task)
     if (S->cfg.flags & AES_SERVER_PIN_THREADS) S->sched_cpu = pin_thread(0);
     double last_work = S->now(), last_query = 0;
     std::vector<aes_server_completion> finished;
@@ -856,7 +989,7 @@ static void scheduler_resident(aes_server* S) {
         if (!finished.empty()) {  // one hand-over per pass, not one per request
             {
                 SchedLock lk(S, kLockDone);
-                S->done.insert(S->done.end(), finished.begin(), finished.end());
+                S->done.push(finished.data(), finished.size());
             }
             {
                 SchedLock lk(S, kLockStats);
@@ -1020,14 +1153,15 @@ static int enqueue(aes_server* S, const aes_server_request& r, double arrival) {
 }
 
 static void producer_main(aes_server* S) {
+    pthread_setname_np(pthread_self(), "gbaes-replay");
     if (S->cfg.flags & AES_SERVER_PIN_THREADS) S->producer_cpu = pin_thread(1);
     const double start = S->now();
     S->replay_start = start;
     // Lateness diagnostics: the thread's involuntary switches are read every
     // 16th hand-over and at any hand-over 20 us late or more.
     double cpu0 = 0;
-    long inv_begin = 0, inv_prev = 0;
-    ThreadWatch::usage(&cpu0, &inv_begin);
+    long inv_begin = 0, inv_prev = 0, flt_begin = 0;
+    ThreadWatch::usage(&cpu0, &inv_begin, nullptr, &flt_begin);
     inv_prev = inv_begin;
     uint64_t handovers = 0;
     double late_max = 0, late_at = 0;
@@ -1045,7 +1179,7 @@ static void producer_main(aes_server* S) {
         } else {
             aes_server_completion c{r.id, rc, 0, t, t, S->now()};
             std::lock_guard<std::mutex> lk(S->out_mu);
-            S->done.push_back(c);
+            S->done.push(&c, 1);
         }
     };
     for (size_t i = 0; i < n;) {
@@ -1087,10 +1221,11 @@ static void producer_main(aes_server* S) {
     }
     {
         double cpu;
-        long inv;
-        ThreadWatch::usage(&cpu, &inv);
+        long inv, flt;
+        ThreadWatch::usage(&cpu, &inv, nullptr, &flt);
         std::lock_guard<std::mutex> lk(S->stats_mu);
         aes_server_diag& d = S->diag;
+        d.producer_minflt += (uint64_t)(flt - flt_begin);
         if (late_max > 1e-9 * d.producer_late_max_ns) {
             d.producer_late_max_ns = (uint64_t)(1e9 * late_max);
             d.producer_late_at_ns = (uint64_t)(1e9 * late_at);
@@ -1288,6 +1423,8 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
         destroy_server(S);
         return nullptr;
     }
+    S->done.set_page_locked(!S->dryrun);
+    S->done.reserve(kCompletionsAhead);  // (short of memory: completions then take pages as they come)
     S->stats.budget_bytes = cfg.budget_bytes;
     S->diag.sched_cpu = -1;
     S->diag.producer_cpu = -1;
@@ -1342,6 +1479,10 @@ int aes_server_replay(aes_server* S, const aes_server_request* reqs, size_t n) {
             S->diag.producer_check_at_ns = (uint64_t)(1e9 * check_at);
         }
     }
+    {
+        std::lock_guard<std::mutex> lk(S->out_mu);
+        S->done.reserve(n + kCompletionsAhead);  // every completion of the replay lands on a page made now
+    }
     clear_error();
     S->producer_stop.store(false);
     S->producer_running.store(true);
@@ -1369,12 +1510,9 @@ int aes_server_drain(aes_server* S, double timeout_s) {
 int aes_server_poll(aes_server* S, aes_server_completion* out, size_t max) {
     if (!S || S->magic != kServerMagic) return fail(AES_ERR_ARG, "invalid aes_server");
     if (max && !out) return fail(AES_ERR_ARG, "out is NULL");
+    if (max > 0x7FFFFFFF) max = 0x7FFFFFFF;  // (the count is returned as an int)
     std::lock_guard<std::mutex> lk(S->out_mu);
-    const size_t n = std::min(max, S->done.size());
-    if (n > 0x7FFFFFFF) return fail(AES_ERR_ARG, "poll at most 2^31-1 completions at a time");
-    std::copy(S->done.begin(), S->done.begin() + n, out);
-    S->done.erase(S->done.begin(), S->done.begin() + n);
-    return (int)n;
+    return (int)S->done.pop(out, max);
 }
 
 int aes_server_get_stats(aes_server* S, aes_server_stats* out) {

@@ -135,6 +135,7 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
                                           int(diag["sched_worst_window_majflt"])],
             "sched_worst_window_at_s": diag["sched_worst_window_at_ns"] / 1e9,
             "sched_invol": int(diag["sched_invol"]),
+            "page_faults": [int(diag["sched_minflt"]), int(diag["producer_minflt"])],
             "lock_wait_max_us": {k: v / 1e3 for k, v in zip(("inbox", "done", "stats"), diag["lock_wait_max_ns"])},
             "lock_wait_at_s": {k: v / 1e9 for k, v in zip(("inbox", "done", "stats"), diag["lock_wait_at_ns"])},
             "cuda_call_max_us": diag["cuda_call_max_ns"] / 1e3,

@@ -104,6 +104,50 @@ def test_open_loop_replay_and_producer_stop(gbaes):
     srv.close()
 
 
+def test_completions_oldest_first_across_chunks(gbaes):
+    """The completion store (chunks of 16,384, made ahead and reused) hands out
+    every completion once, oldest first, when polls of odd sizes interleave with
+    new requests across chunk boundaries."""
+    rng = np.random.default_rng(5)
+    srv = gbaes.Server(keyset(gbaes), dryrun=True)
+    buf = np.zeros(7777, gbaes.COMPLETION)
+    total, parts = 0, []
+    for burst in range(4):
+        reqs = fake_requests(gbaes, 12_345, rng, max_blocks=4)  # all due at once
+        reqs["id"] += total
+        total += len(reqs)
+        srv.replay(reqs)
+        srv.replay_join()
+        srv.drain(30.0)
+        for _ in range(burst + 1):  # leaves some behind for the next burst
+            parts.append(srv.poll(buf.size, out=buf).copy())
+    parts.append(srv.poll_all())
+    done = np.concatenate(parts)
+    assert len(done) == total and (done["status"] == 0).all()
+    assert np.array_equal(np.sort(done["id"]), np.arange(total))
+    assert np.all(np.diff(done["done_s"]) >= 0)  # observation order
+    assert srv.poll().size == 0
+    srv.close()
+
+
+@pytest.mark.parametrize("resident", [False, True])
+def test_scheduler_page_faults_do_not_grow_with_completions(gbaes, resident):
+    """A replay's completions land in memory made (and touched) before it
+    starts: the scheduler and replay threads take a handful of page faults for
+    100,000 requests, not one per page of completions (~1,000 pages)."""
+    rng = np.random.default_rng(2)
+    kw = dict(threads=64, blocks_per_thread=1) if resident else {}
+    srv = gbaes.Server(keyset(gbaes), dryrun=True, resident=resident, **kw)
+    reqs = fake_requests(gbaes, 100_000, rng, max_blocks=4, rate=400_000.0)
+    srv.replay(reqs)
+    srv.replay_join()
+    srv.drain(30.0)
+    d = srv.diag()
+    assert len(srv.poll_all()) == 100_000
+    assert d["sched_minflt"] < 200 and d["producer_minflt"] < 200, d
+    srv.close()
+
+
 def test_cancel_waiting_requests(gbaes):
     # Budget for one request at a time: later submissions wait for admission
     # and can be cancelled; the running one cannot.
