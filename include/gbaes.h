@@ -393,7 +393,10 @@ int aes_server_submit(aes_server* server, const aes_server_request* req);
  * queueing delay is counted).  The array is copied and every request is
  * checked during this call (the caller must keep its buffers valid until the
  * requests complete); a request that fails its check completes with its error
- * at its arrival time.  One replay at a time. */
+ * at its arrival time.  The call also makes room for all n completions
+ * (40 bytes each, page-locked host memory, kept by the server until it is
+ * destroyed), so the server's threads do not allocate while the replay runs.
+ * One replay at a time. */
 int aes_server_replay(aes_server* server, const aes_server_request* reqs, size_t n);
 
 /* Waits for the replay thread (stop_early != 0: ends it after its current request). */
