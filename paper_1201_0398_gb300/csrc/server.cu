@@ -58,6 +58,174 @@ struct Pending {
     double arrival;  // seconds on the server clock
 };
 
+// Page-locked memory for the data the server's threads touch on every pass.
+// The kernel's memory compaction moves ordinary pages, and a thread that
+// touches a page while it is being moved sleeps until the move ends (seen on
+// the GB300 machine: scheduler and replay thread both in migration_entry_wait for
+// 43-97 ms, every request in flight waiting with them); pages page-locked by
+// CUDA are never moved.  HotPool hands out blocks in power-of-two size classes
+// (64 B .. 2 MiB) carved from 4 MiB page-locked chunks and keeps freed blocks
+// for reuse, so after warm-up the containers below allocate nothing new;
+// larger blocks get page-locked allocations of their own.  In a dry run (no
+// GPU) it uses ordinary heap memory, touched when carved.
+class HotPool {
+  public:
+    explicit HotPool(bool page_locked) : page_locked_(page_locked) {}
+    HotPool(const HotPool&) = delete;
+    HotPool& operator=(const HotPool&) = delete;
+    ~HotPool() {
+        for (const auto& c : chunks_) raw_free(c.first, c.second);
+        for (const auto& b : big_) raw_free(b.first, b.second);
+    }
+
+    bool page_locked() const { return page_locked_; }
+
+    // bytes of page-locked memory (heap memory if that fails or !page_locked),
+    // every page touched; *locked says which.  nullptr when out of memory.
+    static void* raw_alloc(size_t bytes, bool page_locked, bool* locked) {
+        void* p = nullptr;
+        *locked = false;
+        if (page_locked) {
+            if (cudaHostAlloc(&p, bytes, cudaHostAllocDefault) == cudaSuccess) {
+                *locked = true;
+                return p;
+            }
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (posix_memalign(&p, 4096, bytes) != 0) return nullptr;
+        memset(p, 0, bytes);
+        return p;
+    }
+    static void raw_free(void* p, bool locked) {
+        if (locked)
+            cudaFreeHost(p);
+        else
+            free(p);
+    }
+
+    void* allocate(size_t bytes) {
+        const int c = size_class(bytes);
+        std::lock_guard<std::mutex> lk(mu_);
+        if (c < 0) {
+            bool locked = false;
+            void* p = raw_alloc((bytes + 4095) & ~(size_t)4095, page_locked_, &locked);
+            if (p) big_.emplace_back(p, locked);
+            return p;
+        }
+        if (free_[c]) {
+            void* p = free_[c];
+            free_[c] = *static_cast<void**>(p);
+            return p;
+        }
+        const size_t sz = (size_t)64 << c;
+        if (left_ < sz) {
+            bool locked = false;
+            void* chunk = raw_alloc(kChunkBytes, page_locked_, &locked);
+            if (!chunk) return nullptr;
+            chunks_.emplace_back(chunk, locked);
+            cur_ = static_cast<uint8_t*>(chunk);
+            left_ = kChunkBytes;
+        }
+        void* p = cur_;
+        cur_ += sz;
+        left_ -= sz;
+        return p;
+    }
+
+    void deallocate(void* p, size_t bytes) noexcept {
+        if (!p) return;
+        const int c = size_class(bytes);
+        std::lock_guard<std::mutex> lk(mu_);
+        if (c < 0) {
+            for (size_t i = 0; i < big_.size(); ++i)
+                if (big_[i].first == p) {
+                    raw_free(p, big_[i].second);
+                    big_[i] = big_.back();
+                    big_.pop_back();
+                    return;
+                }
+            return;
+        }
+        *static_cast<void**>(p) = free_[c];
+        free_[c] = p;
+    }
+
+  private:
+    static constexpr int kClasses = 16;               // 64 B << 0 .. 15
+    static constexpr size_t kChunkBytes = (size_t)4 << 20;
+    static int size_class(size_t bytes) {
+        int c = 0;
+        while (c < kClasses && ((size_t)64 << c) < bytes) ++c;
+        return c < kClasses ? c : -1;
+    }
+    std::mutex mu_;
+    void* free_[kClasses] = {};  // freed blocks per class, linked through their first word
+    std::vector<std::pair<void*, bool>> chunks_, big_;  // (memory, page-locked)
+    uint8_t* cur_ = nullptr;
+    size_t left_ = 0;
+    bool page_locked_;
+};
+
+// Standard allocator over a HotPool.
+template <class T>
+struct HotAlloc {
+    using value_type = T;
+    HotPool* pool;
+    explicit HotAlloc(HotPool* p) : pool(p) {}
+    template <class U>
+    HotAlloc(const HotAlloc<U>& o) : pool(o.pool) {}
+    T* allocate(size_t n) {
+        void* p = pool->allocate(n * sizeof(T));
+        if (!p) throw std::bad_alloc();
+        return static_cast<T*>(p);
+    }
+    void deallocate(T* p, size_t n) noexcept { pool->deallocate(p, n * sizeof(T)); }
+    template <class U>
+    bool operator==(const HotAlloc<U>& o) const { return pool == o.pool; }
+    template <class U>
+    bool operator!=(const HotAlloc<U>& o) const { return pool != o.pool; }
+};
+
+template <class T>
+using HotVec = std::vector<T, HotAlloc<T>>;
+template <class T>
+using HotDeque = std::deque<T, HotAlloc<T>>;
+
+// Page-locks the top of the calling thread's stack (where its frames and its
+// thread-local data live) for the thread's life, so compaction cannot move
+// those pages either.  No-op in a dry run or if the driver refuses.
+class PinnedStackTop {
+  public:
+    explicit PinnedStackTop(bool page_locked) {
+        if (!page_locked) return;
+        pthread_attr_t attr;
+        if (pthread_getattr_np(pthread_self(), &attr) != 0) return;
+        void* addr = nullptr;
+        size_t size = 0;
+        const int rc = pthread_attr_getstack(&attr, &addr, &size);
+        pthread_attr_destroy(&attr);
+        if (rc != 0 || !addr || size < 2 * kPage) return;
+        const uintptr_t lo = (uintptr_t)addr, hi = (lo + size) & ~(uintptr_t)(kPage - 1);
+        const uintptr_t base = hi - std::min<uintptr_t>(kTop, hi - lo - kPage);
+        if (cudaHostRegister((void*)base, hi - base, cudaHostRegisterDefault) == cudaSuccess) {
+            base_ = (void*)base;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    ~PinnedStackTop() {
+        if (base_) cudaHostUnregister(base_);
+    }
+    PinnedStackTop(const PinnedStackTop&) = delete;
+    PinnedStackTop& operator=(const PinnedStackTop&) = delete;
+
+  private:
+    static constexpr uintptr_t kPage = 4096;
+    static constexpr uintptr_t kTop = 256 << 10;
+    void* base_ = nullptr;
+};
+
 // Completions waiting for aes_server_poll: a FIFO of fixed-size chunks.
 // Chunks are made ahead of use (reserve: page-locked when a GPU is present, so
 // the kernel's memory compaction cannot move them, and every page touched when
@@ -194,11 +362,12 @@ class CompletionFifo {
 constexpr size_t kCompletionsAhead = 4 * CompletionFifo::kChunk;
 
 struct Slot {
+    explicit Slot(HotPool* pool) : reqs(HotAlloc<Pending>(pool)) {}
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     uint8_t* dev_buf = nullptr;
     uint8_t* host_buf = nullptr;
-    std::vector<Pending> reqs;
+    HotVec<Pending> reqs;
     double launch_s = 0;
     uint64_t bytes = 0;
     bool busy = false;
@@ -285,13 +454,25 @@ struct ThreadWatch {
 
 using namespace gbaes;
 
+// Lives in page-locked memory itself (aes_server_create), like its hot containers.
 struct aes_server {
+    explicit aes_server(bool page_locked)
+        : pool(page_locked),
+          keys(HotAlloc<aes_ctx>(&pool)),
+          key_ptrs(HotAlloc<const aes_ctx*>(&pool)),
+          inbox(HotAlloc<Pending>(&pool)),
+          queue(HotAlloc<Pending>(&pool)),
+          replay_reqs(HotAlloc<aes_server_request>(&pool)),
+          replay_rc(HotAlloc<int32_t>(&pool)),
+          rinflight{HotDeque<ResItem>(HotAlloc<ResItem>(&pool)), HotDeque<ResItem>(HotAlloc<ResItem>(&pool))} {}
+
     uint32_t magic = 0;
     aes_server_config cfg{};
     int device = 0;
     bool dryrun = false;
-    std::vector<aes_ctx> keys;          // host copies (key sizes, schedules)
-    std::vector<const aes_ctx*> key_ptrs;
+    HotPool pool;                       // the containers below allocate from it
+    HotVec<aes_ctx> keys;               // host copies (key sizes, schedules)
+    HotVec<const aes_ctx*> key_ptrs;
     uint4* dev_keys = nullptr;          // resident schedules: slot 2k = enc, 2k+1 = dec
     int* status = nullptr;
     size_t slot_cap = 0;
@@ -300,11 +481,11 @@ struct aes_server {
 
     std::mutex in_mu;
     std::condition_variable in_cv;  // wakes an idle scheduler
-    std::vector<Pending> inbox;
+    HotVec<Pending> inbox;
     std::atomic<size_t> inbox_n{0};  // inbox.size(), readable without the lock
     std::vector<uint64_t> cancels;  // ids to cancel if still waiting for admission
     std::atomic<size_t> cancels_n{0};
-    std::deque<Pending> queue;  // scheduler thread only
+    HotDeque<Pending> queue;  // scheduler thread only
     uint64_t inflight_bytes = 0;  // scheduler thread only
     uint64_t batch_counter = 0;   // scheduler thread only
 
@@ -322,8 +503,8 @@ struct aes_server {
     std::atomic<bool> producer_running{false};
     std::thread scheduler;
     std::thread producer;
-    std::vector<aes_server_request> replay_reqs;
-    std::vector<int32_t> replay_rc;  // each replayed request's check, made when the replay starts
+    HotVec<aes_server_request> replay_reqs;
+    HotVec<int32_t> replay_rc;  // each replayed request's check, made when the replay starts
     double replay_start = 0;
 
     // Resident mode (scheduler thread only, except where noted).
@@ -342,7 +523,7 @@ struct aes_server {
     uint64_t ritems[2] = {0, 0};      // requests published per direction
     uint64_t rrel_tiles[2] = {0, 0};  // tiles below this are finished: their ring slots are free
     uint64_t rrel_items[2] = {0, 0};  // requests up to this sequence number are finished
-    std::deque<ResItem> rinflight[2];
+    HotDeque<ResItem> rinflight[2];
     bool rlive = false;               // a kernel (or its dry-run stand-in) is running
     bool rstopping = false;           // its stop word is set: nothing is published until it has ended
     double rstop_s = 0;               // when the stop word was set
@@ -370,6 +551,7 @@ struct aes_server {
     aes_server_diag diag{};       // published copy (stats_mu)
     int sched_cpu = -1, producer_cpu = -1;  // CPU each thread is pinned to (AES_SERVER_PIN_THREADS), or -1
     bool sched_slept = false;     // scheduler: its last idle wait slept on the condition variable
+    bool self_locked = false;     // this object's own memory is page-locked
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -477,7 +659,7 @@ static void publish_diagnostics(aes_server* S) {
     d.sched_cpu = S->sched_cpu;
 }
 
-static void complete(aes_server* S, std::vector<Pending>& reqs, int status, double launch_s, double done_s) {
+static void complete(aes_server* S, HotVec<Pending>& reqs, int status, double launch_s, double done_s) {
     {
         SchedLock lk(S, kLockDone);
         for (const Pending& p : reqs) {
@@ -571,7 +753,7 @@ static bool take_inbox(aes_server* S) {
         S->inbox_hold_max = std::max(S->inbox_hold_max, S->now() - t);
     }
     if (!cancels.empty()) {  // only requests not yet admitted can be cancelled
-        std::vector<Pending> gone;
+        HotVec<Pending> gone(HotAlloc<Pending>(&S->pool));
         for (auto it = S->queue.begin(); it != S->queue.end();) {
             if (std::find(cancels.begin(), cancels.end(), it->r.id) != cancels.end()) {
                 gone.push_back(*it);
@@ -608,6 +790,7 @@ static bool idle_wait(aes_server* S, bool idle) {
 static void scheduler_main(aes_server* S) {
     if (!S->dryrun) cudaSetDevice(S->device);
     pthread_setname_np(pthread_self(), "gbaes-sched");  // (names for ps, top and /proc/<pid>/task)
+    const PinnedStackTop stack_top(!S->dryrun);
     if (S->cfg.flags & AES_SERVER_PIN_THREADS) S->sched_cpu = pin_thread(0);
     for (;;) {
         S->sched_watch.pass(S->now(), !S->sched_slept);
@@ -865,7 +1048,7 @@ static void fail_resident_inflight(aes_server* S, int status) {
     for (int d = 0; d < 2; ++d) {
         for (ResItem& it : S->rinflight[d]) {
             if (it.done) continue;
-            std::vector<Pending> one{it.p};
+            HotVec<Pending> one(1, it.p, HotAlloc<Pending>(&S->pool));
             S->inflight_bytes -= it.bytes;
             complete(S, one, status, it.launch_s, t);
         }
@@ -942,9 +1125,10 @@ static bool publish(aes_server* S, const Pending& p, uint64_t bytes, double now)
 static void scheduler_resident(aes_server* S) {
     if (!S->dryrun) cudaSetDevice(S->device);
     pthread_setname_np(pthread_self(), "gbaes-sched");  // (names for ps, top and /proc/<pid>/task)
+    const PinnedStackTop stack_top(!S->dryrun);
     if (S->cfg.flags & AES_SERVER_PIN_THREADS) S->sched_cpu = pin_thread(0);
     double last_work = S->now(), last_query = 0;
-    std::vector<aes_server_completion> finished;
+    HotVec<aes_server_completion> finished(HotAlloc<aes_server_completion>(&S->pool));
     const double idle_s = 1e-6 * S->cfg.resident_idle_us;
     // Normally well before the kernel's own bound (80%); later in tests of the recovery.
     const double restart_s = 1e-5 * S->cfg.resident_restart_pct * S->cfg.resident_lifetime_ms;
@@ -966,7 +1150,7 @@ static void scheduler_resident(aes_server* S) {
             if ((w >> 40) != cq_lap(S->rcq_head, S->rargs.cq_log2)) break;  // not written in this lap yet
             ++S->rcq_head;
             const int d = (int)((w >> 39) & 1u);
-            std::deque<ResItem>& q = S->rinflight[d];
+            HotDeque<ResItem>& q = S->rinflight[d];
             if (q.empty()) continue;  // (not in flight)
             const uint64_t seq = q.front().seq + (((w & kCqSeqMask) - q.front().seq) & kCqSeqMask);
             if (seq - q.front().seq >= q.size()) continue;  // (not in flight)
@@ -1033,7 +1217,7 @@ static void scheduler_resident(aes_server* S) {
             const Pending& p = S->queue.front();
             const uint64_t b = request_bytes(p.r);
             if (p.r.nblocks == 0) {
-                std::vector<Pending> one{p};
+                HotVec<Pending> one(1, p, HotAlloc<Pending>(&S->pool));
                 S->queue.pop_front();
                 const double t = S->now();
                 complete(S, one, AES_OK, t, t);
@@ -1043,7 +1227,7 @@ static void scheduler_resident(aes_server* S) {
             if (S->inflight_bytes + b > S->cfg.budget_bytes) break;
             if (S->batch_counter == S->fault_batch.load()) {
                 ++S->batch_counter;
-                std::vector<Pending> one{p};
+                HotVec<Pending> one(1, p, HotAlloc<Pending>(&S->pool));
                 S->queue.pop_front();
                 const double t = S->now();
                 complete(S, one, fail(AES_ERR_DEVICE, "injected fault"), t, t);
@@ -1154,6 +1338,7 @@ static int enqueue(aes_server* S, const aes_server_request& r, double arrival) {
 
 static void producer_main(aes_server* S) {
     pthread_setname_np(pthread_self(), "gbaes-replay");
+    const PinnedStackTop stack_top(!S->dryrun);
     if (S->cfg.flags & AES_SERVER_PIN_THREADS) S->producer_cpu = pin_thread(1);
     const double start = S->now();
     S->replay_start = start;
@@ -1168,7 +1353,7 @@ static void producer_main(aes_server* S) {
     long late_invol = 0;
     // Every request was checked when the replay was started (no driver call here).
     auto check = [&](size_t i) { return S->replay_rc[i]; };
-    std::vector<Pending> due_now;
+    HotVec<Pending> due_now(HotAlloc<Pending>(&S->pool));
     const size_t n = S->replay_reqs.size();
     // Hands request r (already checked: rc) to the scheduler's batch, or
     // completes it at once with its error.
@@ -1261,7 +1446,9 @@ static void destroy_server(aes_server* S) {
         if (S->rargs.cq_next) cudaFree(S->rargs.cq_next);
         if (S->rstream) cudaStreamDestroy(S->rstream);
     }
-    delete S;
+    const bool locked = S->self_locked;
+    S->~aes_server();
+    HotPool::raw_free(S, locked);
 }
 
 static bool pow2(uint32_t x) { return x && !(x & (x - 1)); }
@@ -1381,11 +1568,15 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
             fail(AES_ERR_ARG, "keys[%zu] is not a valid aes_ctx", i);
             return nullptr;
         }
-    aes_server* S = new (std::nothrow) aes_server();
-    if (!S) {
+    const bool page_locked = (cfg.flags & AES_SERVER_DRYRUN) == 0;
+    bool locked = false;
+    void* mem = HotPool::raw_alloc(sizeof(aes_server), page_locked, &locked);
+    if (!mem) {
         fail(AES_ERR_NOMEM, "out of host memory");
         return nullptr;
     }
+    aes_server* S = new (mem) aes_server(page_locked);
+    S->self_locked = locked;
     S->cfg = cfg;
     S->dryrun = (cfg.flags & AES_SERVER_DRYRUN) != 0;
     S->resident = (cfg.flags & AES_SERVER_RESIDENT) != 0;
@@ -1393,7 +1584,8 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
     S->keys.assign(nkeys, aes_ctx{});
     for (size_t i = 0; i < nkeys; ++i) S->keys[i] = *keys[i];
     for (size_t i = 0; i < nkeys; ++i) S->key_ptrs.push_back(&S->keys[i]);
-    if (!S->resident) S->slots.resize(cfg.nstreams);
+    if (!S->resident)
+        for (int i = 0; i < cfg.nstreams; ++i) S->slots.emplace_back(&S->pool);
     const uint64_t tb = 32ull * cfg.blocks_per_thread;
     S->slot_cap = 256 + (((size_t)cfg.max_batch_msgs * sizeof(MsgDev) + 255) & ~(size_t)255) +
                   4 * (size_t)(cfg.max_batch_blocks / tb + 8) + 4;

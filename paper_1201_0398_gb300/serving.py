@@ -14,15 +14,53 @@ from . import COMPLETION, REQUEST, Key, Server, ecb_ex, workloads
 
 GiB = 1 << 30
 
+_VM_KEYS = ("pgmigrate_success", "compact_migrate_scanned", "compact_daemon_migrate_scanned")
+
+
+def _vmstat() -> dict:
+    """The kernel's page-migration and compaction counters (empty if unreadable)."""
+    try:
+        with open("/proc/vmstat") as f:
+            return {k: int(v) for k, v in (line.split() for line in f) if k in _VM_KEYS}
+    except OSError:
+        return {}
+
+
+def _wait_compaction_quiet(max_s: float, quiet_s: float = 1.0) -> float:
+    """Waits (at most max_s) until the kernel has migrated no page for quiet_s:
+    memory compaction set off by the setup (GBs of buffers just allocated) moves
+    pages under the server's threads and code, and a thread that touches a page
+    being moved sleeps until the move ends.  Returns the seconds waited."""
+    import time
+
+    t0 = time.monotonic()
+    last, since = _vmstat(), t0
+    if not last:
+        return 0.0
+    while time.monotonic() - t0 < max_s:
+        time.sleep(0.1)
+        cur = _vmstat()
+        if cur != last:
+            last, since = cur, time.monotonic()
+        elif time.monotonic() - since >= quiet_s:
+            break
+    return time.monotonic() - t0
+
 
 def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8 << 30, nkeys: int = 1024,
         nstreams: int = 4, threads: int = 0, blocks_per_thread: int = 0, max_batch_msgs: int = 4096,
         pool_bytes: int = GiB, check_last: int = 1000, seed: int = workloads.SEED_SERVE,
         resident: bool = False, pin_threads: bool = False, poll_every_s: float = 0.0,
-        host_payloads: bool = False) -> dict:
+        host_payloads: bool = False, warmup_s: float = 0.2, settle_max_s: float = 10.0) -> dict:
     """host_payloads: the input pool and the output ring live in page-locked host
     memory instead of device memory (the kernels read and write them over the host
-    link); the ring then holds twice the in-flight budget, at least 1 GiB."""
+    link); the ring then holds twice the in-flight budget, at least 1 GiB.
+    warmup_s: the first warmup_s seconds of the schedule run first on a separate
+    server with the same settings (untimed; every code path of the server, the
+    driver calls and the kernel's launch, end and relaunch have then run once).
+    settle_max_s: then wait at most this long for the kernel's memory compaction
+    to go quiet before the measured replay (reported as host_memory.settle_s,
+    with the pages migrated during the replay)."""
     import torch
 
     w = workloads.serve_workload(rate=rate, duration_s=duration_s, nkeys=nkeys, seed=seed)
@@ -52,9 +90,24 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
     reqs["arrival_s"] = w.arrival_s
 
     torch.cuda.synchronize()  # inputs complete before the first request
-    srv = Server(keys, budget_bytes=budget_bytes, nstreams=nstreams, threads=threads,
-                 blocks_per_thread=blocks_per_thread, max_batch_msgs=max_batch_msgs, resident=resident,
-                 pin_threads=pin_threads)
+
+    def make_server():
+        return Server(keys, budget_bytes=budget_bytes, nstreams=nstreams, threads=threads,
+                      blocks_per_thread=blocks_per_thread, max_batch_msgs=max_batch_msgs, resident=resident,
+                      pin_threads=pin_threads)
+
+    if warmup_s > 0:
+        k = max(1, int(np.searchsorted(w.arrival_s, warmup_s)))
+        wsrv = make_server()
+        wsrv.replay(reqs[:k])
+        wsrv.replay_join()
+        wsrv.drain(120.0)
+        wsrv.poll_all()
+        wsrv.close()
+        torch.cuda.synchronize()
+    settle_s = _wait_compaction_quiet(settle_max_s) if settle_max_s > 0 else 0.0
+    vm0 = _vmstat()
+    srv = make_server()
     parts = []
     polling = poll_every_s > 0
     if polling:  # a client that takes its completions as they come (the server's queue stays short)
@@ -78,6 +131,7 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
     srv.replay(reqs)
     srv.replay_join()
     srv.drain(120.0)
+    vm1 = _vmstat()
     if polling:
         stop.set()
         th.join()
@@ -124,6 +178,11 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
         "max_queue": int(stats["max_queue"]), "max_inflight_bytes": int(stats["max_inflight_bytes"]),
         "budget_bytes": int(budget_bytes), "nstreams": nstreams, "shape": f"{threads or 512}x{blocks_per_thread or (2 if resident else 1)}",
         "checked_alone": int(len(idx)), "mismatches": mismatches,
+        "host_memory": {"warmup_s": warmup_s, "settle_s": round(settle_s, 2),
+                        "pages_migrated_during_replay": (vm1.get("pgmigrate_success", 0) - vm0.get("pgmigrate_success", 0))
+                        if vm0 else None,
+                        "compaction_pages_scanned_during_replay":
+                            sum(vm1.get(k, 0) - vm0.get(k, 0) for k in _VM_KEYS[1:]) if vm0 else None},
         "host_threads": {
             "pinned_cpus": [int(diag["sched_cpu"]), int(diag["producer_cpu"])],
             "sched_passes": int(diag["sched_passes"]),
