@@ -826,7 +826,7 @@ def run_serve_sweep(args):
             keep = ("mode", "value", "offered_gbs", "requests", "completed_ok", "p50_ms", "p99_ms", "p999_ms",
                     "max_ms", "p50_queue_ms", "p50_service_ms", "max_queue", "max_inflight_bytes", "shape",
                     "mismatches", "mean_batch_msgs", "p50_service_ms", "p99_service_ms", "host_threads",
-                    "kernel_launches", "payloads")
+                    "kernel_launches", "payloads", "host_memory")
             print(json.dumps({"sweep": "serving", "rate": rate, "seconds": args.serve_sweep_seconds,
                               **{k: r[k] for k in keep if k in r}}), flush=True)
 

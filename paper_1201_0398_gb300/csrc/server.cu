@@ -58,10 +58,42 @@ struct Pending {
     double arrival;  // seconds on the server clock
 };
 
+// `bytes` of host memory with every page touched: page-locked by CUDA through
+// `device`'s context (device >= 0; heap memory if the driver refuses) or plain
+// heap memory (device < 0).  *locked says which; nullptr when out of memory.
+// The caller's current device is left as it was.
+static void* alloc_host(size_t bytes, int device, bool* locked) {
+    void* p = nullptr;
+    *locked = false;
+    if (device >= 0) {
+        int prev = -1;
+        const bool swap = cudaGetDevice(&prev) == cudaSuccess && prev != device;
+        if (swap) cudaSetDevice(device);
+        if (cudaHostAlloc(&p, bytes, cudaHostAllocPortable) == cudaSuccess) {
+            *locked = true;
+        } else {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (swap) cudaSetDevice(prev);
+        if (p) return p;
+    }
+    if (posix_memalign(&p, 4096, bytes) != 0) return nullptr;
+    memset(p, 0, bytes);
+    return p;
+}
+
+static void free_host(void* p, bool locked) {
+    if (locked)
+        cudaFreeHost(p);
+    else
+        free(p);
+}
+
 // Page-locked memory for the data the server's threads touch on every pass.
 // The kernel's memory compaction moves ordinary pages, and a thread that
-// touches a page while it is being moved sleeps until the move ends (seen on
-// the GB300 machine: scheduler and replay thread both in migration_entry_wait for
+// touches a page while it is being moved sleeps until the move ends (measured
+// on a GB300 node: scheduler and replay thread both in migration_entry_wait for
 // 43-97 ms, every request in flight waiting with them); pages page-locked by
 // CUDA are never moved.  HotPool hands out blocks in power-of-two size classes
 // (64 B .. 2 MiB) carved from 4 MiB page-locked chunks and keeps freed blocks
@@ -70,38 +102,12 @@ struct Pending {
 // GPU) it uses ordinary heap memory, touched when carved.
 class HotPool {
   public:
-    explicit HotPool(bool page_locked) : page_locked_(page_locked) {}
+    explicit HotPool(int device) : device_(device) {}  // device < 0: heap memory (dry run)
     HotPool(const HotPool&) = delete;
     HotPool& operator=(const HotPool&) = delete;
     ~HotPool() {
-        for (const auto& c : chunks_) raw_free(c.first, c.second);
-        for (const auto& b : big_) raw_free(b.first, b.second);
-    }
-
-    bool page_locked() const { return page_locked_; }
-
-    // bytes of page-locked memory (heap memory if that fails or !page_locked),
-    // every page touched; *locked says which.  nullptr when out of memory.
-    static void* raw_alloc(size_t bytes, bool page_locked, bool* locked) {
-        void* p = nullptr;
-        *locked = false;
-        if (page_locked) {
-            if (cudaHostAlloc(&p, bytes, cudaHostAllocDefault) == cudaSuccess) {
-                *locked = true;
-                return p;
-            }
-            cudaGetLastError();
-            p = nullptr;
-        }
-        if (posix_memalign(&p, 4096, bytes) != 0) return nullptr;
-        memset(p, 0, bytes);
-        return p;
-    }
-    static void raw_free(void* p, bool locked) {
-        if (locked)
-            cudaFreeHost(p);
-        else
-            free(p);
+        for (const auto& c : chunks_) free_host(c.first, c.second);
+        for (const auto& b : big_) free_host(b.first, b.second);
     }
 
     void* allocate(size_t bytes) {
@@ -109,7 +115,7 @@ class HotPool {
         std::lock_guard<std::mutex> lk(mu_);
         if (c < 0) {
             bool locked = false;
-            void* p = raw_alloc((bytes + 4095) & ~(size_t)4095, page_locked_, &locked);
+            void* p = alloc_host((bytes + 4095) & ~(size_t)4095, device_, &locked);
             if (p) big_.emplace_back(p, locked);
             return p;
         }
@@ -121,7 +127,7 @@ class HotPool {
         const size_t sz = (size_t)64 << c;
         if (left_ < sz) {
             bool locked = false;
-            void* chunk = raw_alloc(kChunkBytes, page_locked_, &locked);
+            void* chunk = alloc_host(kChunkBytes, device_, &locked);
             if (!chunk) return nullptr;
             chunks_.emplace_back(chunk, locked);
             cur_ = static_cast<uint8_t*>(chunk);
@@ -140,7 +146,7 @@ class HotPool {
         if (c < 0) {
             for (size_t i = 0; i < big_.size(); ++i)
                 if (big_[i].first == p) {
-                    raw_free(p, big_[i].second);
+                    free_host(p, big_[i].second);
                     big_[i] = big_.back();
                     big_.pop_back();
                     return;
@@ -164,7 +170,7 @@ class HotPool {
     std::vector<std::pair<void*, bool>> chunks_, big_;  // (memory, page-locked)
     uint8_t* cur_ = nullptr;
     size_t left_ = 0;
-    bool page_locked_;
+    int device_;
 };
 
 // Standard allocator over a HotPool.
@@ -247,7 +253,7 @@ class CompletionFifo {
         for (Chunk* c : spare_) drop(c);
     }
 
-    void set_page_locked(bool v) { page_locked_ = v; }
+    void set_device(int device) { device_ = device; }  // page-locked chunks through this device; < 0: heap
     size_t size() const { return size_; }
 
     // Room for n more completions than are held now, made ahead of use.
@@ -257,7 +263,7 @@ class CompletionFifo {
         const size_t free_in_tail = live_.empty() ? 0 : kChunk - tail_;
         size_t room = free_in_tail + kChunk * spare_.size();
         while (room < n) {
-            Chunk* c = make(page_locked_);
+            Chunk* c = make(device_);
             if (!c) return false;
             spare_.push_back(c);
             room += kChunk;
@@ -278,7 +284,7 @@ class CompletionFifo {
                     k = spare_.back();
                     spare_.pop_back();
                 } else {
-                    k = make(false);  // (no spare left: a plain allocation, touched as it fills)
+                    k = make(-1);  // (no spare left: a plain allocation made here)
                     if (!k) return false;
                 }
                 live_.push_back(k);
@@ -323,38 +329,21 @@ class CompletionFifo {
         aes_server_completion e[kChunk];
     };
 
-    static Chunk* make(bool page_locked) {
-        void* p = nullptr;
-        if (page_locked) {
-            if (cudaHostAlloc(&p, sizeof(Chunk), cudaHostAllocDefault) != cudaSuccess) {
-                cudaGetLastError();
-                p = nullptr;
-                page_locked = false;
-            }
-        }
-        if (!p) {
-            p = malloc(sizeof(Chunk));
-            if (!p) return nullptr;
-        }
-        memset(p, 0, sizeof(Chunk));  // every page touched now, not when a completion lands on it
-        Chunk* c = static_cast<Chunk*>(p);
-        c->page_locked = page_locked;
+    static Chunk* make(int device) {
+        bool locked = false;
+        Chunk* c = static_cast<Chunk*>(alloc_host(sizeof(Chunk), device, &locked));
+        if (c) c->page_locked = locked;
         return c;
     }
 
-    static void drop(Chunk* c) {
-        if (c->page_locked)
-            cudaFreeHost(c);
-        else
-            free(c);
-    }
+    static void drop(Chunk* c) { free_host(c, c->page_locked); }
 
     std::vector<Chunk*> live_;   // oldest first; the last one is being filled
     std::vector<Chunk*> spare_;  // made ahead, or emptied by pop
     size_t head_ = 0;            // next to pop, in live_.front()
     size_t tail_ = 0;            // next free entry in live_.back()
     size_t size_ = 0;
-    bool page_locked_ = false;
+    int device_ = -1;
 };
 
 // Completions made up front when a server starts, and kept spare beyond a
@@ -456,8 +445,8 @@ using namespace gbaes;
 
 // Lives in page-locked memory itself (aes_server_create), like its hot containers.
 struct aes_server {
-    explicit aes_server(bool page_locked)
-        : pool(page_locked),
+    explicit aes_server(int host_device)
+        : pool(host_device),
           keys(HotAlloc<aes_ctx>(&pool)),
           key_ptrs(HotAlloc<const aes_ctx*>(&pool)),
           inbox(HotAlloc<Pending>(&pool)),
@@ -1338,6 +1327,7 @@ static int enqueue(aes_server* S, const aes_server_request& r, double arrival) {
 
 static void producer_main(aes_server* S) {
     pthread_setname_np(pthread_self(), "gbaes-replay");
+    if (!S->dryrun) cudaSetDevice(S->device);  // (the stack registration and pool chunks use its context)
     const PinnedStackTop stack_top(!S->dryrun);
     if (S->cfg.flags & AES_SERVER_PIN_THREADS) S->producer_cpu = pin_thread(1);
     const double start = S->now();
@@ -1448,7 +1438,7 @@ static void destroy_server(aes_server* S) {
     }
     const bool locked = S->self_locked;
     S->~aes_server();
-    HotPool::raw_free(S, locked);
+    free_host(S, locked);
 }
 
 static bool pow2(uint32_t x) { return x && !(x & (x - 1)); }
@@ -1568,14 +1558,19 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
             fail(AES_ERR_ARG, "keys[%zu] is not a valid aes_ctx", i);
             return nullptr;
         }
-    const bool page_locked = (cfg.flags & AES_SERVER_DRYRUN) == 0;
+    int host_device = -1;  // page-locked server data through this device's context (none in a dry run)
+    if ((cfg.flags & AES_SERVER_DRYRUN) == 0 && cudaGetDevice(&host_device) != cudaSuccess) {
+        cudaGetLastError();
+        fail(AES_ERR_CUDA, "server setup: no current device");
+        return nullptr;
+    }
     bool locked = false;
-    void* mem = HotPool::raw_alloc(sizeof(aes_server), page_locked, &locked);
+    void* mem = alloc_host(sizeof(aes_server), host_device, &locked);
     if (!mem) {
         fail(AES_ERR_NOMEM, "out of host memory");
         return nullptr;
     }
-    aes_server* S = new (mem) aes_server(page_locked);
+    aes_server* S = new (mem) aes_server(host_device);
     S->self_locked = locked;
     S->cfg = cfg;
     S->dryrun = (cfg.flags & AES_SERVER_DRYRUN) != 0;
@@ -1615,7 +1610,7 @@ aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const ae
         destroy_server(S);
         return nullptr;
     }
-    S->done.set_page_locked(!S->dryrun);
+    S->done.set_device(S->dryrun ? -1 : S->device);
     S->done.reserve(kCompletionsAhead);  // (short of memory: completions then take pages as they come)
     S->stats.budget_bytes = cfg.budget_bytes;
     S->diag.sched_cpu = -1;
