@@ -98,7 +98,8 @@ static void free_host(void* p, bool locked) {
 // CUDA are never moved.  HotPool hands out blocks in power-of-two size classes
 // (64 B .. 2 MiB) carved from 4 MiB page-locked chunks and keeps freed blocks
 // for reuse, so after warm-up the containers below allocate nothing new;
-// larger blocks get page-locked allocations of their own.  In a dry run (no
+// larger blocks get page-locked allocations of their own, also kept for reuse
+// until the pool goes (nothing is unpinned while the server runs).  In a dry run (no
 // GPU) it uses ordinary heap memory, touched when carved.
 class HotPool {
   public:
@@ -107,16 +108,25 @@ class HotPool {
     HotPool& operator=(const HotPool&) = delete;
     ~HotPool() {
         for (const auto& c : chunks_) free_host(c.first, c.second);
-        for (const auto& b : big_) free_host(b.first, b.second);
+        for (const Big& b : big_) free_host(b.p, b.locked);
     }
 
     void* allocate(size_t bytes) {
         const int c = size_class(bytes);
         std::lock_guard<std::mutex> lk(mu_);
-        if (c < 0) {
+        if (c < 0) {  // the smallest kept block that fits, else a new one
+            const size_t want = (bytes + 4095) & ~(size_t)4095;
+            size_t pick = big_.size();
+            for (size_t i = 0; i < big_.size(); ++i)
+                if (!big_[i].used && big_[i].bytes >= want && (pick == big_.size() || big_[i].bytes < big_[pick].bytes))
+                    pick = i;
+            if (pick < big_.size()) {
+                big_[pick].used = true;
+                return big_[pick].p;
+            }
             bool locked = false;
-            void* p = alloc_host((bytes + 4095) & ~(size_t)4095, device_, &locked);
-            if (p) big_.emplace_back(p, locked);
+            void* p = alloc_host(want, device_, &locked);
+            if (p) big_.push_back(Big{p, want, locked, true});
             return p;
         }
         if (free_[c]) {
@@ -143,14 +153,9 @@ class HotPool {
         if (!p) return;
         const int c = size_class(bytes);
         std::lock_guard<std::mutex> lk(mu_);
-        if (c < 0) {
-            for (size_t i = 0; i < big_.size(); ++i)
-                if (big_[i].first == p) {
-                    free_host(p, big_[i].second);
-                    big_[i] = big_.back();
-                    big_.pop_back();
-                    return;
-                }
+        if (c < 0) {  // kept for reuse: freeing page-locked memory can wait for the device
+            for (Big& b : big_)
+                if (b.p == p) b.used = false;
             return;
         }
         *static_cast<void**>(p) = free_[c];
@@ -167,7 +172,13 @@ class HotPool {
     }
     std::mutex mu_;
     void* free_[kClasses] = {};  // freed blocks per class, linked through their first word
-    std::vector<std::pair<void*, bool>> chunks_, big_;  // (memory, page-locked)
+    struct Big {
+        void* p;
+        size_t bytes;
+        bool locked, used;
+    };
+    std::vector<std::pair<void*, bool>> chunks_;  // (memory, page-locked)
+    std::vector<Big> big_;                        // blocks above 2 MiB, in use or kept for reuse
     uint8_t* cur_ = nullptr;
     size_t left_ = 0;
     int device_;
