@@ -111,9 +111,11 @@ class HotPool {
         for (const Big& b : big_) free_host(b.p, b.locked);
     }
 
+    // (New memory is made with the lock released: the driver call can take
+    // milliseconds, and the other thread's allocations need not wait for it.)
     void* allocate(size_t bytes) {
         const int c = size_class(bytes);
-        std::lock_guard<std::mutex> lk(mu_);
+        std::unique_lock<std::mutex> lk(mu_);
         if (c < 0) {  // the smallest kept block that fits, else a new one
             const size_t want = (bytes + 4095) & ~(size_t)4095;
             size_t pick = big_.size();
@@ -124,29 +126,37 @@ class HotPool {
                 big_[pick].used = true;
                 return big_[pick].p;
             }
+            lk.unlock();
             bool locked = false;
             void* p = alloc_host(want, device_, &locked);
+            lk.lock();
             if (p) big_.push_back(Big{p, want, locked, true});
             return p;
         }
-        if (free_[c]) {
-            void* p = free_[c];
-            free_[c] = *static_cast<void**>(p);
-            return p;
-        }
         const size_t sz = (size_t)64 << c;
-        if (left_ < sz) {
+        for (;;) {
+            if (free_[c]) {
+                void* p = free_[c];
+                free_[c] = *static_cast<void**>(p);
+                return p;
+            }
+            if (left_ >= sz) {
+                void* p = cur_;
+                cur_ += sz;
+                left_ -= sz;
+                return p;
+            }
+            lk.unlock();
             bool locked = false;
             void* chunk = alloc_host(kChunkBytes, device_, &locked);
+            lk.lock();
             if (!chunk) return nullptr;
             chunks_.emplace_back(chunk, locked);
-            cur_ = static_cast<uint8_t*>(chunk);
-            left_ = kChunkBytes;
+            if (left_ < sz) {  // (another thread may have made one meanwhile: the rest of this one stays unused)
+                cur_ = static_cast<uint8_t*>(chunk);
+                left_ = kChunkBytes;
+            }
         }
-        void* p = cur_;
-        cur_ += sz;
-        left_ -= sz;
-        return p;
     }
 
     void deallocate(void* p, size_t bytes) noexcept {
