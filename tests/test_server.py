@@ -613,6 +613,37 @@ def test_dryrun_unpinned_threads_report_no_cpu(gbaes):
     assert d["sched_cpu"] == -1 and d["producer_cpu"] == -1
 
 
+def test_server_threads_are_named(gbaes):
+    """The scheduler and replay threads carry names (gbaes-sched, gbaes-replay) for ps, top and
+    /proc/<pid>/task, where a watchdog finds them."""
+    import os
+    import time
+
+    task = "/proc/self/task"
+    if not os.path.isdir(task):
+        pytest.skip("no /proc task list")
+
+    def names():
+        out = set()
+        for t in os.listdir(task):
+            try:
+                with open(f"{task}/{t}/comm") as f:
+                    out.add(f.read().strip())
+            except OSError:
+                pass
+        return out
+
+    srv = gbaes.Server(keyset(gbaes), dryrun=True)
+    rng = np.random.default_rng(8)
+    srv.replay(fake_requests(gbaes, 2000, rng, rate=10_000.0))  # ~0.2 s of arrivals
+    time.sleep(0.05)
+    seen = names()
+    srv.replay_join()
+    srv.drain(10.0)
+    srv.close()
+    assert {"gbaes-sched", "gbaes-replay"} <= seen, seen
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("resident", (False, True))
 def test_server_with_payloads_in_page_locked_host_memory(gbaes, resident):
