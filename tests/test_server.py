@@ -613,6 +613,43 @@ def test_dryrun_unpinned_threads_report_no_cpu(gbaes):
     assert d["sched_cpu"] == -1 and d["producer_cpu"] == -1
 
 
+@pytest.mark.parametrize("resident", [False, True])
+def test_concurrent_submitters_and_replay(gbaes, resident):
+    """Four client threads submit while a replay runs and completions are polled:
+    the server's shared queues and its memory pool take allocations from several
+    threads at once; every request completes exactly once."""
+    import threading
+
+    kw = dict(threads=64, blocks_per_thread=1) if resident else {}
+    srv = gbaes.Server(keyset(gbaes), dryrun=True, resident=resident, **kw)
+    rng = np.random.default_rng(9)
+    reqs = fake_requests(gbaes, 20_000, rng, max_blocks=4, rate=200_000.0)
+    reqs["id"] += 1_000_000
+    srv.replay(reqs)
+
+    def client(c):
+        for i in range(3000):
+            srv.submit(c * 10_000 + i, i % 4, 1 << 20, 2 << 20, 1 + i % 3, decrypt=bool(i & 1))
+
+    ths = [threading.Thread(target=client, args=(c,)) for c in range(4)]
+    for t in ths:
+        t.start()
+    got = []
+    buf = np.zeros(4096, gbaes.COMPLETION)
+    while any(t.is_alive() for t in ths):
+        got.append(srv.poll(buf.size, out=buf).copy())
+    for t in ths:
+        t.join()
+    srv.replay_join()
+    srv.drain(30.0)
+    got.append(srv.poll_all())
+    done = np.concatenate(got)
+    want = np.concatenate([np.arange(c * 10_000, c * 10_000 + 3000) for c in range(4)] + [reqs["id"]])
+    assert (done["status"] == 0).all()
+    assert np.array_equal(np.sort(done["id"]), np.sort(want))
+    srv.close()
+
+
 def test_server_threads_are_named(gbaes):
     """The scheduler and replay threads carry names (gbaes-sched, gbaes-replay) for ps, top and
     /proc/<pid>/task, where a watchdog finds them."""
