@@ -330,6 +330,8 @@ typedef struct aes_server_stats {
     uint64_t max_batch_msgs;
     uint64_t budget_bytes;
     uint64_t recovered_tiles;    /* resident mode: tiles re-published after the kernel's own bound ended it */
+    uint64_t lost_completions;   /* completions dropped because no host memory was left to hold them
+                                    (aes_server_poll never returns these; 0 unless memory ran out) */
 } aes_server_stats;
 
 /* Host-thread diagnostics of a server, for latency tails.  Times in ns; the

@@ -473,7 +473,7 @@ class _ServerConfig(ctypes.Structure):
 class _ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "rejected", "batches",
                                                "max_inflight_bytes", "max_queue", "max_batch_msgs", "budget_bytes",
-                                               "recovered_tiles")]
+                                               "recovered_tiles", "lost_completions")]
 
 
 class _ServerDiag(ctypes.Structure):

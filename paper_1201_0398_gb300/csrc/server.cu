@@ -295,9 +295,10 @@ class CompletionFifo {
         return true;
     }
 
-    // Appends n completions.  Returns false (appending what fits) only when a
-    // chunk cannot be allocated.
-    bool push(const aes_server_completion* c, size_t n) {
+    // Appends n completions; returns how many were stored (fewer only when no
+    // host memory is left for a chunk).
+    size_t push(const aes_server_completion* c, size_t n) {
+        const size_t n0 = n;
         while (n) {
             if (live_.empty() || tail_ == kChunk) {
                 Chunk* k = nullptr;
@@ -306,7 +307,7 @@ class CompletionFifo {
                     spare_.pop_back();
                 } else {
                     k = make(-1);  // (no spare left: a plain allocation made here)
-                    if (!k) return false;
+                    if (!k) return n0 - n;
                 }
                 live_.push_back(k);
                 tail_ = 0;
@@ -318,7 +319,7 @@ class CompletionFifo {
             c += m;
             n -= m;
         }
-        return true;
+        return n0;
     }
 
     // Moves up to max of the oldest completions to out; returns how many.
@@ -501,6 +502,7 @@ struct aes_server {
 
     std::mutex out_mu;
     CompletionFifo done;  // completions waiting for aes_server_poll (under out_mu)
+    std::atomic<uint64_t> lost_completions{0};  // not stored: no host memory left (aes_server_stats)
 
     std::mutex stats_mu;
     aes_server_stats stats{};
@@ -680,7 +682,7 @@ static void complete(aes_server* S, HotVec<Pending>& reqs, int status, double la
             c.arrival_s = p.arrival;
             c.launch_s = launch_s;
             c.done_s = done_s;
-            S->done.push(&c, 1);
+            if (S->done.push(&c, 1) != 1) S->lost_completions.fetch_add(1);
         }
     }
     {
@@ -1183,7 +1185,8 @@ static void scheduler_resident(aes_server* S) {
         if (!finished.empty()) {  // one hand-over per pass, not one per request
             {
                 SchedLock lk(S, kLockDone);
-                S->done.push(finished.data(), finished.size());
+                const size_t kept = S->done.push(finished.data(), finished.size());
+                if (kept != finished.size()) S->lost_completions.fetch_add(finished.size() - kept);
             }
             {
                 SchedLock lk(S, kLockStats);
@@ -1375,7 +1378,7 @@ static void producer_main(aes_server* S) {
         } else {
             aes_server_completion c{r.id, rc, 0, t, t, S->now()};
             std::lock_guard<std::mutex> lk(S->out_mu);
-            S->done.push(&c, 1);
+            if (S->done.push(&c, 1) != 1) S->lost_completions.fetch_add(1);
         }
     };
     for (size_t i = 0; i < n;) {
@@ -1728,6 +1731,7 @@ int aes_server_get_stats(aes_server* S, aes_server_stats* out) {
     if (!out) return fail(AES_ERR_ARG, "out is NULL");
     std::lock_guard<std::mutex> lk(S->stats_mu);
     *out = S->stats;
+    out->lost_completions = S->lost_completions.load();
     return AES_OK;
 }
 

@@ -145,6 +145,7 @@ def test_scheduler_page_faults_do_not_grow_with_completions(gbaes, resident):
     d = srv.diag()
     assert len(srv.poll_all()) == 100_000
     assert d["sched_minflt"] < 200 and d["producer_minflt"] < 200, d
+    assert srv.stats()["lost_completions"] == 0
     srv.close()
 
 
