@@ -175,7 +175,7 @@ def run(rate: float = 200_000.0, duration_s: float = 10.0, budget_bytes: int = 8
         "p99_service_ms": float(np.percentile(service, 99) * 1e3),
         "mean_batch_msgs": float(n / max(1, len(batches))),
         ("kernel_launches" if resident else "batches"): int(stats["batches"]),
-        "max_queue": int(stats["max_queue"]), "max_inflight_bytes": int(stats["max_inflight_bytes"]),
+        "max_queue": int(stats["max_queue"]), "lost_completions": int(stats["lost_completions"]), "max_inflight_bytes": int(stats["max_inflight_bytes"]),
         "budget_bytes": int(budget_bytes), "nstreams": nstreams, "shape": f"{threads or 512}x{blocks_per_thread or (2 if resident else 1)}",
         "checked_alone": int(len(idx)), "mismatches": mismatches,
         "host_memory": {"warmup_s": warmup_s, "settle_s": round(settle_s, 2),
