@@ -382,7 +382,12 @@ int aes_server_get_diag(aes_server* server, aes_server_diag* out);
 
 /* Creates a server on the current device with nkeys resident key contexts
  * (copied; the caller may free them afterwards) and starts its scheduler
- * thread.  config may be NULL for the defaults.  NULL on error. */
+ * thread.  config may be NULL for the defaults.  NULL on error.
+ * The server keeps the data its threads touch on every pass (its own state,
+ * queues, key copies, replay arrays, completions and the top of each thread's
+ * stack) in page-locked host memory, which the kernel's memory compaction
+ * cannot move: ~7 MiB to start, plus ~100 bytes per request of each replay,
+ * held until aes_server_destroy. */
 aes_server* aes_server_create(const aes_ctx* const* keys, size_t nkeys, const aes_server_config* config);
 
 /* Queues one request (arrival = now).  Checks its pointers and sizes on the
