@@ -831,7 +831,7 @@ def run_serve_sweep(args):
                               **{k: r[k] for k in keep if k in r}}), flush=True)
 
 
-PROFILE_CASES = ("table", "table1g", "bitsliced", "batch", "sweep", "singles")
+PROFILE_CASES = ("table", "table1g", "bitsliced", "bitsliced1g", "batch", "sweep", "singles")
 
 
 def run_profile_case(args):
@@ -845,6 +845,7 @@ def run_profile_case(args):
                  for single-pass DRAM-byte captures at the bench size only
       bitsliced  256 MiB, AES-128 encryption + decryption, then AES-256 encryption +
                  decryption, bitsliced kernel
+      bitsliced1g the same four launches at 1 GiB (2 GiB on the device), the bench's size
       batch      10,000 messages, 16 B - 1 MiB (~0.95 GB), one batched launch each
       sweep      one AES-128 encryption per size, 4 KiB - 256 MiB: table (size-dispatched),
                  compact tables (up to 64 MiB), replicated tables, bitsliced
@@ -859,11 +860,12 @@ def run_profile_case(args):
 
     g.load()
     case, warm, launches = args.profile_case, args.profile_warmup, args.profile_launches
-    if case in ("table", "table1g", "bitsliced"):
-        kid = g.KERNEL_BITSLICED if case == "bitsliced" else g.KERNEL_TABLE
-        size = {"table": 256 << 20, "table1g": GiB, "bitsliced": 256 << 20}[case]
+    if case in ("table", "table1g", "bitsliced", "bitsliced1g"):
+        kid = g.KERNEL_BITSLICED if case.startswith("bitsliced") else g.KERNEL_TABLE
+        size = {"table": 256 << 20, "table1g": GiB, "bitsliced": 256 << 20, "bitsliced1g": GiB}[case]
         ops = {"table": [(128, False), (256, True)],
                "bitsliced": [(128, False), (128, True), (256, False), (256, True)],
+               "bitsliced1g": [(128, False), (128, True), (256, False), (256, True)],
                "table1g": [(b, d) for b in BITS for d in (False, True)]}[case]
         x = workloads.device_bytes(1, size)
         y = torch.empty_like(x)
