@@ -61,7 +61,7 @@ LOOKUPS_PER_CLK_PER_SM = 32  # 32 banks x 4 B: one conflict-free 32-bit lookup p
 ALU_LANES_PER_CLK_PER_SM = 64  # integer ALU pipe: 4 SM sub-partitions x 16 lanes
 # The bitsliced kernel's integer-ALU instructions per 16-byte block, (Nr, decrypt) -> lane-ops, counted by ncu
 # (ALU-pipe utilisation x 2 warp instructions per clock per SM x active cycles x SMs x 32 / blocks) in
-# profiles/bitsliced_kernel_ecb_256MiB_ncu_full.md.
+# profiles/bitsliced_kernel_ecb_256MiB_1GiB_ncu_full.md.
 BITSLICED_ALU_OPS_PER_BLOCK = {(10, 0): 562.5, (10, 1): 639.5, (14, 0): 752.3, (14, 1): 860.3}
 
 
